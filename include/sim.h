@@ -1,0 +1,229 @@
+/*
+ * sim.h — C ABI of the GB300 SIM-M library (libsim.so).
+ *
+ * SIM-M (Huang, Sun, Yang, "A Multilevel Spectral Indicator Method for
+ * Eigenvalues of Large Non-Hermitian Matrices") finds every eigenvalue of the
+ * pencil A x = λ B x inside a region R of the complex plane (Sec. 1, Eq.
+ * AxLambdaBx) to a precision h0, together with its multiplicity (Sec. 3.4).
+ * The calls follow the algorithm's signature SIM-M(A, B, R, f, h0, ε, δ0, m, n0)
+ * of Sec. 3.5:
+ *
+ *   sim_create        — A, B (steps' inputs)                         Sec. 3.5
+ *   sim_set_region    — R and f; steps 1-3 (first shift, initial
+ *                       squares, shift association with new Krylov
+ *                       spaces)                                        Sec. 3.5
+ *   sim_solve_level   — one pass of step 5 (one level of Sec. 3.3)
+ *   sim_eigenvalues   — step 6-7 (merge, output)
+ *   sim_multiplicity  — Sec. 3.4
+ *
+ * Conventions shared by every call:
+ *  - Complex numbers are complex128 stored as interleaved (re, im) doubles.
+ *  - Every call returns a sim_status and never throws; a handle's last error
+ *    message is available from sim_last_error().
+ *  - The library copies what it needs (A, B, f) into its own device memory;
+ *    the caller keeps ownership of every pointer it passes and may free it
+ *    when the call returns.  Outputs go to caller-allocated host arrays.
+ *  - All device work is issued on the CUDA stream given to sim_create (NULL
+ *    means the legacy default stream).  Calls return when their outputs are
+ *    ready.
+ *  - The handle is a state machine: create -> set_region -> solve_level (until
+ *    done) -> eigenvalues -> multiplicity.  A call out of order returns
+ *    SIM_ERR_BAD_STATE; sim_set_region may be called again to start over.
+ *  - One handle must not be used by two host threads at once.
+ */
+#ifndef SIM_GB300_H
+#define SIM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sim_ctx* sim_handle;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_ERR_INVALID_ARG = 1,    /* bad pointer, size, CSR structure or option */
+    SIM_ERR_BAD_STATE = 2,      /* call out of order */
+    SIM_ERR_CUDA = 3,           /* a CUDA runtime call failed (message names it) */
+    SIM_ERR_OOM = 4,            /* device allocation failed */
+    SIM_ERR_NOT_CONVERGED = 5,  /* an inner solve hit its iteration cap */
+    SIM_ERR_CAPACITY = 6,       /* output buffer too small; *count holds the size needed */
+    SIM_ERR_LIMIT = 7           /* a level would exceed max_squares, or too many shifts */
+} sim_status;
+
+typedef enum {
+    SIM_FP64 = 0,   /* factorisation, inner solves and Krylov bases in complex128 */
+    SIM_MIXED = 1   /* complex64 factorisation with FP64 GMRES refinement of each
+                       shifted solve; FP64 Gram–Schmidt, Hessenberg solves and tests */
+} sim_precision;
+
+/* A square sparse matrix in CSR form: row_ptr[n+1], col_idx[nnz] (0-based,
+ * each row's columns strictly increasing), values[2*nnz] (complex128).
+ * on_device != 0 means the three arrays are device pointers. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const double* values;
+    int32_t on_device;
+} sim_csr;
+
+/* Parameters of Sec. 3.5 plus the readings this library fixes.  Get the
+ * defaults from sim_default_options() and change fields as needed. */
+typedef struct {
+    int32_t m;                /* Krylov dimension (Sec. 3.5: 50) */
+    int32_t n0;               /* coarse quadrature rule size; the fine rule has 2*n0
+                                 nodes.  Only n0 = 4 is supported. */
+    double delta0;            /* indicator threshold δ0 (Sec. 3.1: 1/20) */
+    double eps;               /* residual tolerance ε of Def. 3.1 (1e-8) */
+    double h0;                /* precision: the final squares have side <= h0 (1e-6) */
+    double init_side;         /* side of the initial squares; 0 => min(width, height) of R */
+    double shift_sep;         /* min separation, in initial sides, of shifts made in one round (4) */
+    int32_t max_shift_rounds; /* rounds of step 3 (16) */
+    int32_t max_shifts;       /* capacity for Krylov spaces (256) */
+    double breakdown_tol;     /* Arnoldi stops when h_{j+1,j} <= tol * ||H||_F (1e-14) */
+    double merge_radius;      /* clusters whose estimates are closer are joined (0) */
+    int32_t mult_k;           /* random vectors for multiplicity (8); doubled while rank == k */
+    int32_t mult_kmax;        /* upper limit of k (64) */
+    double mult_tol;          /* singular values > mult_tol * largest count toward the rank (1e-6) */
+    int32_t mult_nodes;       /* quadrature nodes on a cluster's circle (16) */
+    uint64_t mult_seed;       /* Philox4x64-10 key word 0 for the multiplicity vectors */
+    int32_t residual_scale;   /* 0: residual relative to ||y|| (default); 1: relative to beta */
+    int64_t max_squares;      /* a level holding more squares is an error (4,000,000) */
+    sim_precision precision;  /* SIM_FP64 (default) or SIM_MIXED */
+    double inner_tol;         /* relative residual target of each shifted solve (1e-12) */
+    int32_t inner_restart;    /* GMRES restart length (8) */
+    int32_t inner_max_iter;   /* GMRES iteration cap per solve (64) */
+} sim_options;
+
+/* Counters of the last set_region .. multiplicity sequence. */
+typedef struct {
+    int64_t n, nnz_A, nnz_B;
+    int32_t block_size, num_blocks;      /* block-tridiagonal layout of A - σB */
+    int32_t num_shifts;
+    int32_t levels_total, levels_done;
+    int64_t squares_evaluated;           /* summed over levels */
+    int64_t projected_solves;            /* Hessenberg solves (quadrature points) */
+    int64_t inner_solves;                /* shifted solves (A - σB) x = r completed */
+    int64_t gmres_iterations;            /* summed over inner solves */
+    int32_t max_gmres_iterations;        /* worst single inner solve */
+    int64_t unresolvable_final;          /* final squares not resolvable (warnings of step 6) */
+    int64_t final_squares;
+    int64_t clusters;
+    double max_inner_residual;           /* worst relative residual of an inner solve */
+    double t_factor_ms, t_krylov_ms, t_levels_ms, t_merge_ms, t_mult_ms;
+} sim_stats_t;
+
+/* Fills *opt with the defaults listed above.  opt must not be NULL. */
+void sim_default_options(sim_options* opt);
+
+/* Creates a handle for the pencil (A, B).  B == NULL means B = I.  A and B must
+ * have the same n; B may be any CSR (a diagonal B is detected and stored as a
+ * vector).  The library determines the band half-width w = max |i - j| over the
+ * nonzeros of A and B and stores A - σB for each shift as a block tridiagonal
+ * matrix with blocks of side w; its memory per shift is about 2·n·w complex
+ * numbers.  stream is a cudaStream_t (NULL = default stream).
+ * Errors: SIM_ERR_INVALID_ARG (NULL pointers, n < 1, unsorted or out-of-range
+ * columns, options out of range), SIM_ERR_OOM, SIM_ERR_CUDA. */
+sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt,
+                      void* stream, sim_handle* out);
+
+/* Sets the search region R = [re_lo, re_hi] × [im_lo, im_hi] and the random
+ * vector f (complex128[n]; f_on_device selects host or device memory; f ==
+ * NULL draws f from Philox4x64-10 with key (seed, 0x53494D4D), vector index 0).
+ * Runs steps 1-3 of Sec. 3.5: the first shift at the centre of R, the initial
+ * squares (side init_side tiling R's bounding box from its lower-left corner,
+ * row-major), and shift rounds: each round tests every unresolved square
+ * against every shift nearest-first, then builds new Krylov spaces at the
+ * centres of unresolved squares spaced at least
+ * max(shift_sep·side, ρ) apart, ρ being the distance from the first shift to
+ * the nearest square it does not resolve.
+ * Errors: SIM_ERR_INVALID_ARG (empty region, bad f), SIM_ERR_LIMIT (more than
+ * max_shifts shifts), SIM_ERR_NOT_CONVERGED, SIM_ERR_OOM, SIM_ERR_CUDA. */
+sim_status sim_set_region(sim_handle h, double re_lo, double re_hi, double im_lo, double im_hi,
+                          const double* f, int32_t f_on_device, uint64_t seed);
+
+/* Evaluates every square of the current level at once (Sec. 3.3, step 5):
+ * the 8 quadrature nodes on each square's circumscribed circle, the projected
+ * solves (I + (σ - z)H_m) y = β e1 (Eq. eq:many) with the residual of Eq.
+ * eq:error, resolvability (Def. 3.1; an unresolvable square retries the other
+ * shifts nearest-first), the indicator of Eq. DeltaSm and the mark
+ * (Ĩ > δ0, or unresolvable).  Marked squares are split into four children for
+ * the next level.  *n_marked receives the number of marked squares, *done is
+ * set to 1 after the last level (side <= h0).
+ * Errors: SIM_ERR_BAD_STATE (no region, or already done), SIM_ERR_LIMIT. */
+sim_status sim_solve_level(sim_handle h, int64_t* n_marked, int32_t* done);
+
+/* Step 6-7: merges the final squares into clusters (8-connected components;
+ * estimate = mean of member centres; estimates closer than merge_radius
+ * joined), keeps clusters whose estimate lies in the closed region, sorts by
+ * (Re, Im) and writes 2*count doubles (re, im) to out.  capacity is in
+ * eigenvalues; capacity 0 (out may be NULL) only returns *count.
+ * Errors: SIM_ERR_BAD_STATE (levels not finished), SIM_ERR_CAPACITY. */
+sim_status sim_eigenvalues(sim_handle h, double* out, int64_t capacity, int64_t* count);
+
+/* Sec. 3.4: the multiplicity of every eigenvalue returned by sim_eigenvalues
+ * (same order): for each shift that resolves clusters, k random vectors
+ * (Philox4x64-10, key (mult_seed, 0x53494D4D), vector indices 1..k), their k
+ * Krylov spaces, P f_i on a mult_nodes-point circle of radius
+ * 2·max(cluster radius, h0) around each estimate, and the number of singular
+ * values of [P f_1 … P f_k] above mult_tol times the largest; k doubles while
+ * the rank equals k, up to mult_kmax.
+ * Errors: SIM_ERR_BAD_STATE (sim_eigenvalues not called), SIM_ERR_CAPACITY. */
+sim_status sim_multiplicity(sim_handle h, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Copies the counters into *out (size = sizeof(sim_stats_t)). */
+sim_status sim_stats(sim_handle h, sim_stats_t* out, size_t size);
+
+/* Per-handle message of the last failed call ("" if none).  Valid until the
+ * next call on the handle.  h == NULL returns the message of the last failed
+ * sim_create. */
+const char* sim_last_error(sim_handle h);
+
+/* Frees every device and host resource of the handle.  NULL is a no-op. */
+void sim_destroy(sim_handle h);
+
+/* ---- Component entry points (the same kernels the pipeline uses) ---------
+ * These expose single steps for parity tests.  All pointers are DEVICE
+ * pointers unless stated; stream may be NULL.  They allocate only the small
+ * scratch they need and free it before returning. */
+
+/* Number of shifts built by the last sim_set_region, and shift s's Krylov data:
+ * sigma (2 doubles), H ((m+1)·m complex128, column-major, leading dim m+1,
+ * HOST memory), beta, and m_eff (< m after an Arnoldi breakdown). */
+sim_status sim_shift_count(sim_handle h, int32_t* count);
+sim_status sim_get_shift(sim_handle h, int32_t s, double* sigma, double* H_host, double* beta,
+                         int32_t* m_eff);
+
+/* Batched projected solves and indicator (Eqs. eq:many, eq:error, DeltaSm)
+ * for `count` squares against one Krylov space given explicitly:
+ * H: (m+1)·m complex128 column-major (ld m+1), sigma = sig_re + i sig_im,
+ * centers: complex128[count], sides: double[count].  Outputs indicator[count]
+ * and rho[count] (the largest residual over the 8 nodes, scaled as
+ * residual_scale says).  1 <= m_eff <= m <= 64. */
+sim_status sim_eval_squares(const double* H, int32_t m, int32_t m_eff, double beta, double sig_re,
+                            double sig_im, const double* centers, const double* sides, int64_t count,
+                            int32_t residual_scale, double* indicator, double* rho, void* stream);
+
+/* y = (A - σB) x for the handle's pencil (complex128[n] vectors). */
+sim_status sim_apply_shifted(sim_handle h, double sig_re, double sig_im, const double* x, double* y);
+
+/* x = (A - σB)^{-1} r by the handle's inner solver (factorisation in the
+ * handle's precision + FP64 GMRES); *iters and *relres report the solve. */
+sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const double* r, double* x,
+                             int32_t* iters, double* relres);
+
+/* Philox4x64-10 complex Gaussian vectors: out[v*n + e] for v < k is element e
+ * of random vector (first + v) with key (seed, 0x53494D4D); complex128. */
+sim_status sim_random_vectors(uint64_t seed, int64_t n, int32_t k, int32_t first, double* out,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIM_GB300_H */

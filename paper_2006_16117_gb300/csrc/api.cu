@@ -1,0 +1,824 @@
+// C ABI of the SIM-M library and the host-side drivers that sequence the
+// kernels: pencil upload, Krylov spaces per shift, the shift rounds of
+// Sec. 3.5 step 3, one level per sim_solve_level (Sec. 3.3), the merge
+// (step 6) and the multiplicity step (Sec. 3.4).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "levels.h"
+#include "mult.h"
+
+using namespace sim;
+
+namespace {
+
+enum State { ST_CREATED = 0, ST_REGION = 1, ST_LEVELS_DONE = 2, ST_EIGS = 3 };
+
+struct Timer {
+    cudaStream_t st;
+    std::chrono::steady_clock::time_point t0;
+    explicit Timer(cudaStream_t s) : st(s) { t0 = std::chrono::steady_clock::now(); }
+    double ms() {
+        cudaStreamSynchronize(st);
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+std::string g_create_error;
+
+}  // namespace
+
+struct sim_ctx {
+    cudaStream_t st = nullptr;
+    sim_options opt{};
+    std::string err;
+    int state = ST_CREATED;
+    Pencil P;
+    DeviceArena arena;
+    // shifts
+    int S = 0;
+    int cap = 0;
+    std::vector<double2> h_sigma;
+    std::vector<void*> factors;
+    double2* d_sigma = nullptr;
+    double2* d_H = nullptr;
+    double* d_beta = nullptr;
+    int* d_meff = nullptr;
+    void** d_fptrs = nullptr;
+    size_t factor_bytes = 0;
+    // input vector
+    double2* d_f = nullptr;
+    // region and levels
+    double re_lo = 0, re_hi = 0, im_lo = 0, im_hi = 0, s1 = 1;
+    int64_t cols = 1, rows = 1;
+    int K = 1, level = 1;
+    int64_t nsq = 0;
+    int cur = 0;
+    int64_t nfinal = 0;
+    double s_final = 1;
+    // clusters (sorted, inside R)
+    std::vector<double2> eig;
+    std::vector<int> cl_shift, cl_size, cl_flag;
+    std::vector<double> cl_radius;
+    std::vector<int> mult;
+    sim_stats_t stats{};
+    InnerStats inner;
+
+    ~sim_ctx() {
+        for (void* p : factors)
+            if (p) cudaFree(p);
+    }
+};
+
+// ---------------------------------------------------------------------------
+namespace {
+
+sim_status fail(sim_ctx* h, sim_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+template <class F> sim_status guarded(sim_ctx* h, F&& f) {
+    try {
+        if (h) h->err.clear();
+        return f();
+    } catch (const CudaError& e) {
+        return fail(h, e.code == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA, e.what);
+    } catch (const std::bad_alloc&) {
+        return fail(h, SIM_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        const std::string w = e.what();
+        if (w.rfind("LIMIT:", 0) == 0) return fail(h, SIM_ERR_LIMIT, w.substr(6));
+        return fail(h, SIM_ERR_CUDA, w);
+    }
+}
+
+struct HostCsr {
+    int64_t n = 0;
+    std::vector<int32_t> rp, ci;
+    std::vector<double2> v;
+};
+
+bool fetch_csr(const sim_csr* A, HostCsr& out, std::string& why) {
+    if (!A || A->n < 1 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->values))) {
+        why = "CSR: NULL pointer or bad size";
+        return false;
+    }
+    out.n = A->n;
+    out.rp.resize(A->n + 1);
+    out.ci.resize(A->nnz);
+    out.v.resize(A->nnz);
+    auto kind = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    SIM_CUDA(cudaMemcpy(out.rp.data(), A->row_ptr, sizeof(int32_t) * (A->n + 1), kind));
+    if (A->nnz) {
+        SIM_CUDA(cudaMemcpy(out.ci.data(), A->col_idx, sizeof(int32_t) * A->nnz, kind));
+        SIM_CUDA(cudaMemcpy(out.v.data(), A->values, sizeof(double2) * A->nnz, kind));
+    }
+    if (out.rp[0] != 0 || out.rp[A->n] != A->nnz) {
+        why = "CSR: row_ptr[0] must be 0 and row_ptr[n] must equal nnz";
+        return false;
+    }
+    for (int64_t i = 0; i < A->n; ++i) {
+        if (out.rp[i + 1] < out.rp[i]) {
+            why = "CSR: row_ptr not monotone";
+            return false;
+        }
+        for (int64_t e = out.rp[i]; e < out.rp[i + 1]; ++e) {
+            if (out.ci[e] < 0 || out.ci[e] >= A->n) {
+                why = "CSR: column index out of range";
+                return false;
+            }
+            if (e > out.rp[i] && out.ci[e] <= out.ci[e - 1]) {
+                why = "CSR: columns of a row must be strictly increasing";
+                return false;
+            }
+            if (!std::isfinite(out.v[e].x) || !std::isfinite(out.v[e].y)) {
+                why = "CSR: non-finite value";
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+void ensure_shift_capacity(sim_ctx* h) {
+    if (h->cap) return;
+    const int cap = h->opt.max_shifts + 1;  // last slot: scratch for component calls
+    const int m = h->opt.m;
+    h->d_sigma = h->arena.get<double2>("sigma", cap);
+    h->d_H = h->arena.get<double2>("H", (int64_t)cap * (m + 1) * m);
+    h->d_beta = h->arena.get<double>("beta", cap);
+    h->d_meff = h->arena.get<int>("meff", cap);
+    h->d_fptrs = h->arena.get<void*>("fptrs", cap);
+    h->factors.assign(cap, nullptr);
+    h->h_sigma.assign(cap, make_double2(0, 0));
+    h->cap = cap;
+}
+
+void* factor_storage(sim_ctx* h, int s) {
+    if (!h->factors[s]) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, h->factor_bytes);
+        if (e != cudaSuccess)
+            throw CudaError{e, "cudaMalloc of a shift factorisation (" + std::to_string(h->factor_bytes) + " bytes)"};
+        h->factors[s] = p;
+        SIM_CUDA(cudaMemcpyAsync(h->d_fptrs + s, &h->factors[s], sizeof(void*), cudaMemcpyHostToDevice, h->st));
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+    }
+    return h->factors[s];
+}
+
+JobSpace make_jobspace(sim_ctx* h, int J, const std::string& tag) {
+    return sim::make_jobspace(h->arena, h->st, J, std::max(1, std::min(h->opt.inner_restart, 32)), h->opt.m, h->P.n, tag);
+}
+
+__global__ void k_copy_start(JobSpace js, int J, const double2* f) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int job = blockIdx.y;
+    if (g >= js.n || job >= J) return;
+    js.vec[(size_t)job * js.vstride + (size_t)VS_RHS * js.n + g] = f[g];
+}
+
+__global__ void k_store_space(JobSpace js, int J, const int* job_shift, double2* H, double* beta, int* meff, int m) {
+    int job = blockIdx.x;
+    if (job >= J) return;
+    int s = job_shift[job];
+    for (int e = threadIdx.x; e < (m + 1) * m; e += blockDim.x) H[(size_t)s * (m + 1) * m + e] = js.H[(size_t)job * (m + 1) * m + e];
+    if (threadIdx.x == 0) {
+        beta[s] = js.beta[job];
+        meff[s] = js.meff[job];
+    }
+}
+
+// Build Krylov spaces for new shifts at the given centres (Sec. 2: factor
+// A - σB, b = (A - σB)^{-1} f, m Arnoldi steps).  Returns false on non-convergence.
+bool build_shifts(sim_ctx* h, const std::vector<double2>& sig) {
+    if (sig.empty()) return true;
+    const int J = (int)sig.size();
+    if (h->S + J > h->opt.max_shifts) throw std::runtime_error("LIMIT:too many shifts (max_shifts)");
+    std::vector<int> ids(J);
+    for (int j = 0; j < J; ++j) {
+        ids[j] = h->S + j;
+        h->h_sigma[ids[j]] = sig[j];
+    }
+    SIM_CUDA(cudaMemcpyAsync(h->d_sigma + h->S, sig.data(), sizeof(double2) * J, cudaMemcpyHostToDevice, h->st));
+    for (int s : ids) factor_storage(h, s);
+    int* d_list = h->arena.get<int>("shift_list", J);
+    SIM_CUDA(cudaMemcpyAsync(d_list, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
+    Timer tf(h->st);
+    factor_shifts(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st);
+    h->stats.t_factor_ms += tf.ms();
+    Timer tk(h->st);
+    JobSpace js = make_jobspace(h, J, "loc_");
+    SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
+    dim3 grid(cdiv_up(h->P.n, 256), J);
+    k_copy_start<<<grid, 256, 0, h->st>>>(js, J, h->d_f);
+    SIM_LAUNCH_CHECK();
+    bool ok = arnoldi(h->P, h->opt, js, h->d_sigma, h->d_fptrs, h->st, h->inner);
+    k_store_space<<<J, 256, 0, h->st>>>(js, J, js.d_jobshift, h->d_H, h->d_beta, h->d_meff, h->opt.m);
+    SIM_LAUNCH_CHECK();
+    SIM_CUDA(cudaStreamSynchronize(h->st));
+    h->S += J;
+    h->stats.t_krylov_ms += tk.ms();
+    return ok;
+}
+
+ShiftTable shift_table(sim_ctx* h) {
+    ShiftTable t;
+    t.H = h->d_H;
+    t.beta = h->d_beta;
+    t.meff = h->d_meff;
+    t.sigma = h->d_sigma;
+    t.S = h->S;
+    t.m = h->opt.m;
+    t.scale = h->opt.residual_scale;
+    t.eps = h->opt.eps;
+    t.delta0 = h->opt.delta0;
+    return t;
+}
+
+double2 center_of(const sim_ctx* h, double s, int64_t ix, int64_t iy) {
+    return make_double2(h->re_lo + ((double)ix + 0.5) * s, h->im_lo + ((double)iy + 0.5) * s);
+}
+
+int num_levels(double s1, double h0) { return s1 > h0 ? (int)std::ceil(std::log2(s1 / h0)) + 1 : 1; }
+
+void sync_stats(sim_ctx* h) {
+    h->stats.num_shifts = h->S;
+    h->stats.inner_solves = h->inner.solves;
+    h->stats.gmres_iterations = h->inner.iters;
+    h->stats.max_gmres_iterations = h->inner.max_iters;
+    h->stats.max_inner_residual = h->inner.worst;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void sim_default_options(sim_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->m = 50;
+    o->n0 = 4;
+    o->delta0 = 0.05;
+    o->eps = 1e-8;
+    o->h0 = 1e-6;
+    o->init_side = 0.0;
+    o->shift_sep = 4.0;
+    o->max_shift_rounds = 16;
+    o->max_shifts = 256;
+    o->breakdown_tol = 1e-14;
+    o->merge_radius = 0.0;
+    o->mult_k = 8;
+    o->mult_kmax = 64;
+    o->mult_tol = 1e-6;
+    o->mult_nodes = 16;
+    o->mult_seed = 0x5EED;
+    o->residual_scale = 0;
+    o->max_squares = 4000000;
+    o->precision = SIM_FP64;
+    o->inner_tol = 1e-12;
+    o->inner_restart = 8;
+    o->inner_max_iter = 64;
+}
+
+sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream, sim_handle* out) {
+    if (!out) return fail(nullptr, SIM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::unique_ptr<sim_ctx> h(new sim_ctx());
+    sim_status s = guarded(nullptr, [&]() -> sim_status {
+        h->st = (cudaStream_t)stream;
+        if (opt) h->opt = *opt;
+        else sim_default_options(&h->opt);
+        const sim_options& o = h->opt;
+        if (o.m < 2 || eval_smem_bytes(o.m) > 220 * 1024 || o.n0 != 4 || !(o.delta0 > 0) || !(o.eps > 0) ||
+            !(o.h0 > 0) || o.max_shifts < 1 || o.max_shifts > SIM_MAX_SHIFTS - 1 || o.mult_k < 1 ||
+            o.mult_kmax < o.mult_k || o.mult_kmax > 64 || o.mult_nodes < 4 || o.mult_nodes > 64 ||
+            !(o.inner_tol > 0) || o.inner_restart < 1 || o.inner_restart > 32 || o.inner_max_iter < 1 ||
+            (o.precision != SIM_FP64 && o.precision != SIM_MIXED) || o.max_squares < 1 ||
+            (o.residual_scale != 0 && o.residual_scale != 1))
+            return fail(nullptr, SIM_ERR_INVALID_ARG, "options out of range (m must be <= 52, n0 must be 4)");
+        HostCsr a, b;
+        std::string why;
+        if (!fetch_csr(A, a, why)) return fail(nullptr, SIM_ERR_INVALID_ARG, "A: " + why);
+        const bool hasB = B != nullptr;
+        if (hasB) {
+            if (!fetch_csr(B, b, why)) return fail(nullptr, SIM_ERR_INVALID_ARG, "B: " + why);
+            if (b.n != a.n) return fail(nullptr, SIM_ERR_INVALID_ARG, "A and B differ in size");
+        }
+        const int64_t n = a.n;
+        // union pattern with A's and B's values
+        std::vector<int32_t> rp(n + 1, 0), ci;
+        std::vector<double2> Ka, Kb;
+        ci.reserve(a.ci.size() + (hasB ? b.ci.size() : n));
+        bool bdiag = true;
+        std::vector<double2> bd(n, make_double2(hasB ? 0.0 : 1.0, 0.0));
+        int64_t kl = 0, ku = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t ea = a.rp[i], eb = hasB ? b.rp[i] : 0;
+            const int64_t fa = a.rp[i + 1], fb = hasB ? b.rp[i + 1] : 0;
+            bool diag_done = hasB;  // B = I contributes the diagonal
+            while (ea < fa || (hasB && eb < fb) || !diag_done) {
+                int64_t ja = ea < fa ? a.ci[ea] : INT64_MAX;
+                int64_t jb = hasB ? (eb < fb ? b.ci[eb] : INT64_MAX) : (diag_done ? INT64_MAX : i);
+                int64_t j = std::min(ja, jb);
+                double2 va = make_double2(0, 0), vb = make_double2(0, 0);
+                if (ja == j) va = a.v[ea++];
+                if (jb == j) {
+                    if (hasB) vb = b.v[eb++];
+                    else {
+                        vb = make_double2(1.0, 0.0);
+                        diag_done = true;
+                    }
+                }
+                if (hasB && jb == j) {
+                    if (j != i && (vb.x != 0 || vb.y != 0)) bdiag = false;
+                    if (j == i) bd[i] = vb;
+                }
+                ci.push_back((int32_t)j);
+                Ka.push_back(va);
+                Kb.push_back(vb);
+                kl = std::max<int64_t>(kl, i - j);
+                ku = std::max<int64_t>(ku, j - i);
+            }
+            rp[i + 1] = (int32_t)ci.size();
+        }
+        Pencil& P = h->P;
+        P.n = n;
+        P.nnz = (int64_t)ci.size();
+        P.T = (int)std::max<int64_t>(1, std::max(kl, ku));
+        P.nb = (int)((n + P.T - 1) / P.T);
+        P.b_kind = hasB ? (bdiag ? 1 : 2) : 0;
+        // couplings to the next block row, column-compressed per block
+        const int T = P.T, nb = P.nb;
+        std::vector<int32_t> up_ptr((size_t)nb * (T + 1), 0), up_row, up_idx;
+        {
+            std::vector<std::vector<std::pair<int32_t, int32_t>>> cols(T);
+            for (int k = 0; k + 1 < nb; ++k) {
+                for (auto& c : cols) c.clear();
+                for (int i = 0; i < T; ++i) {
+                    int64_t g = (int64_t)k * T + i;
+                    if (g >= n) break;
+                    for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
+                        int64_t j = ci[e];
+                        if (j >= (int64_t)(k + 1) * T) cols[j - (int64_t)(k + 1) * T].push_back({i, (int32_t)e});
+                    }
+                }
+                size_t base = (size_t)k * (T + 1);
+                up_ptr[base] = (int32_t)up_row.size();
+                for (int c = 0; c < T; ++c) {
+                    for (auto& pr : cols[c]) {
+                        up_row.push_back(pr.first);
+                        up_idx.push_back(pr.second);
+                    }
+                    up_ptr[base + c + 1] = (int32_t)up_row.size();
+                }
+            }
+        }
+        auto up = [&](const char* name, const void* src, size_t bytes) -> void* {
+            void* d = h->arena.get<unsigned char>(name, (int64_t)bytes);
+            if (bytes) SIM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, h->st));
+            return d;
+        };
+        P.rp = (const int32_t*)up("P_rp", rp.data(), sizeof(int32_t) * rp.size());
+        P.ci = (const int32_t*)up("P_ci", ci.data(), sizeof(int32_t) * ci.size());
+        P.Ka = (const double2*)up("P_Ka", Ka.data(), sizeof(double2) * Ka.size());
+        P.Kb = (const double2*)up("P_Kb", Kb.data(), sizeof(double2) * Kb.size());
+        P.Bdiag = (const double2*)up("P_Bd", bd.data(), sizeof(double2) * bd.size());
+        P.up_ptr = (const int32_t*)up("P_upp", up_ptr.data(), sizeof(int32_t) * up_ptr.size());
+        P.up_row = (const int32_t*)up("P_upr", up_row.data(), sizeof(int32_t) * up_row.size());
+        P.up_idx = (const int32_t*)up("P_upi", up_idx.data(), sizeof(int32_t) * up_idx.size());
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        const size_t cs = o.precision == SIM_FP64 ? sizeof(double2) : sizeof(float2);
+        h->factor_bytes = (size_t)2 * nb * (size_t)T * T * cs;
+        ensure_shift_capacity(h.get());
+        h->d_f = h->arena.get<double2>("f", n);
+        h->stats.n = n;
+        h->stats.nnz_A = (int64_t)a.ci.size();
+        h->stats.nnz_B = hasB ? (int64_t)b.ci.size() : n;
+        h->stats.block_size = T;
+        h->stats.num_blocks = nb;
+        return SIM_OK;
+    });
+    if (s != SIM_OK) return s;
+    *out = h.release();
+    return SIM_OK;
+}
+
+sim_status sim_set_region(sim_handle h, double re_lo, double re_hi, double im_lo, double im_hi, const double* f,
+                          int32_t f_on_device, uint64_t seed) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (!(re_hi > re_lo) || !(im_hi > im_lo) || !std::isfinite(re_lo) || !std::isfinite(re_hi) ||
+            !std::isfinite(im_lo) || !std::isfinite(im_hi))
+            return fail(h, SIM_ERR_INVALID_ARG, "empty or non-finite region");
+        const sim_options& o = h->opt;
+        // reset the state of any previous region
+        for (int s = 0; s < h->cap - 1; ++s) {
+            if (h->factors[s]) {
+                cudaFree(h->factors[s]);
+                h->factors[s] = nullptr;
+            }
+        }
+        h->S = 0;
+        h->eig.clear();
+        h->mult.clear();
+        h->state = ST_CREATED;
+        sim_stats_t keep = h->stats;
+        h->stats = sim_stats_t{};
+        h->stats.n = keep.n;
+        h->stats.nnz_A = keep.nnz_A;
+        h->stats.nnz_B = keep.nnz_B;
+        h->stats.block_size = keep.block_size;
+        h->stats.num_blocks = keep.num_blocks;
+        h->inner = InnerStats{};
+        const int64_t n = h->P.n;
+        if (f) {
+            SIM_CUDA(cudaMemcpyAsync(h->d_f, f, sizeof(double2) * n,
+                                     f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+        } else {
+            random_vectors(seed, n, 1, 0, h->d_f, n, h->st);
+        }
+        h->re_lo = re_lo;
+        h->re_hi = re_hi;
+        h->im_lo = im_lo;
+        h->im_hi = im_hi;
+        const double W = re_hi - re_lo, Hh = im_hi - im_lo;
+        h->s1 = o.init_side > 0 ? o.init_side : std::min(W, Hh);
+        h->cols = std::max<int64_t>(1, (int64_t)std::ceil(W / h->s1 - 1e-12));
+        h->rows = std::max<int64_t>(1, (int64_t)std::ceil(Hh / h->s1 - 1e-12));
+        const int64_t N0 = h->cols * h->rows;
+        if (N0 > o.max_squares) return fail(h, SIM_ERR_LIMIT, "initial tiling exceeds max_squares");
+        h->K = num_levels(h->s1, o.h0);
+        // lattice coordinates at the last level must fit the merge's 64-bit key
+        {
+            const double nx = (double)h->cols * std::ldexp(1.0, h->K - 1), ny = (double)h->rows * std::ldexp(1.0, h->K - 1);
+            if (nx * ny > 9.0e18) return fail(h, SIM_ERR_LIMIT, "region too large for h0 (lattice key overflow)");
+        }
+        std::vector<int64_t> ix(N0), iy(N0);
+        for (int64_t r = 0; r < h->rows; ++r)
+            for (int64_t c = 0; c < h->cols; ++c) {
+                ix[r * h->cols + c] = c;
+                iy[r * h->cols + c] = r;
+            }
+        int64_t* d_ix = h->arena.get<int64_t>("L0_ix", N0);
+        int64_t* d_iy = h->arena.get<int64_t>("L0_iy", N0);
+        int* d_sid = h->arena.get<int>("L0_sid", N0);
+        SIM_CUDA(cudaMemcpyAsync(d_ix, ix.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, h->st));
+        SIM_CUDA(cudaMemcpyAsync(d_iy, iy.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, h->st));
+        SIM_CUDA(cudaMemsetAsync(d_sid, 0, sizeof(int) * N0, h->st));
+        // step 1: the centre of R is the first shift
+        bool ok = build_shifts(h, {make_double2(0.5 * (re_lo + re_hi), 0.5 * (im_lo + im_hi))});
+        // step 3 in rounds
+        std::vector<uint8_t> resolved(N0, 0);
+        std::vector<int> sid(N0, 0);
+        std::vector<uint8_t> hflag(N0);
+        uint8_t* d_todo = h->arena.get<uint8_t>("L0_todo", N0);
+        uint8_t* d_flag = h->arena.get<uint8_t>("L0_flag", N0);
+        double sep = -1.0;
+        Timer tl(h->st);
+        for (int round = 0; round < o.max_shift_rounds; ++round) {
+            std::vector<uint8_t> todo(N0);
+            for (int64_t q = 0; q < N0; ++q) todo[q] = !resolved[q];
+            SIM_CUDA(cudaMemcpyAsync(d_todo, todo.data(), N0, cudaMemcpyHostToDevice, h->st));
+            SIM_CUDA(cudaMemcpyAsync(d_sid, sid.data(), sizeof(int) * N0, cudaMemcpyHostToDevice, h->st));
+            LevelArgs la;
+            la.ix = d_ix;
+            la.iy = d_iy;
+            la.sid = d_sid;
+            la.todo = d_todo;
+            la.flag = d_flag;
+            la.count = N0;
+            la.re_lo = re_lo;
+            la.im_lo = im_lo;
+            la.side = h->s1;
+            eval_level(shift_table(h), la, 1, h->st);
+            SIM_CUDA(cudaMemcpyAsync(hflag.data(), d_flag, N0, cudaMemcpyDeviceToHost, h->st));
+            SIM_CUDA(cudaMemcpyAsync(sid.data(), d_sid, sizeof(int) * N0, cudaMemcpyDeviceToHost, h->st));
+            SIM_CUDA(cudaStreamSynchronize(h->st));
+            h->stats.projected_solves += 8 * (int64_t)std::count(todo.begin(), todo.end(), 1);
+            std::vector<int64_t> un;
+            for (int64_t q = 0; q < N0; ++q) {
+                if (todo[q] && hflag[q] == 0) resolved[q] = 1;
+                if (!resolved[q]) un.push_back(q);
+            }
+            if (un.empty()) break;
+            if (sep < 0) {
+                double rho = INFINITY;
+                const double2 s0 = h->h_sigma[0];
+                for (int64_t q : un) {
+                    double2 c = center_of(h, h->s1, ix[q], iy[q]);
+                    rho = std::min(rho, std::hypot(c.x - s0.x, c.y - s0.y));
+                }
+                sep = std::max(o.shift_sep * h->s1, rho);
+            }
+            std::vector<int64_t> picked;
+            for (int64_t q : un) {
+                double2 c = center_of(h, h->s1, ix[q], iy[q]);
+                bool far = true;
+                for (int64_t p : picked) {
+                    double2 d = center_of(h, h->s1, ix[p], iy[p]);
+                    if (std::hypot(c.x - d.x, c.y - d.y) < sep) {
+                        far = false;
+                        break;
+                    }
+                }
+                if (far) picked.push_back(q);
+            }
+            std::vector<double2> cen;
+            for (size_t t = 0; t < picked.size(); ++t) {
+                cen.push_back(center_of(h, h->s1, ix[picked[t]], iy[picked[t]]));
+                sid[picked[t]] = h->S + (int)t;
+            }
+            ok = build_shifts(h, cen) && ok;
+        }
+        SIM_CUDA(cudaMemcpyAsync(d_sid, sid.data(), sizeof(int) * N0, cudaMemcpyHostToDevice, h->st));
+        h->stats.t_levels_ms += tl.ms();
+        h->nsq = N0;
+        h->cur = 0;
+        h->level = 1;
+        h->stats.levels_total = h->K;
+        h->state = ST_REGION;
+        sync_stats(h);
+        if (!ok) return fail(h, SIM_ERR_NOT_CONVERGED, "an inner shifted solve did not converge");
+        return SIM_OK;
+    });
+}
+
+sim_status sim_solve_level(sim_handle h, int64_t* n_marked, int32_t* done) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (h->state != ST_REGION || h->level > h->K) return fail(h, SIM_ERR_BAD_STATE, "no level to solve");
+        Timer tl(h->st);
+        const int k = h->level;
+        const double side = h->s1 / std::ldexp(1.0, k - 1);
+        const std::string a = "L" + std::to_string(h->cur) + "_", b = "L" + std::to_string(1 - h->cur) + "_";
+        const int64_t N = h->nsq;
+        int64_t* ix = h->arena.get<int64_t>(a + "ix", N);
+        int64_t* iy = h->arena.get<int64_t>(a + "iy", N);
+        int* sid = h->arena.get<int>(a + "sid", N);
+        uint8_t* mark = h->arena.get<uint8_t>("mark", N);
+        uint8_t* flag = h->arena.get<uint8_t>("flag", N);
+        double* ind = h->arena.get<double>("ind", N);
+        LevelArgs la;
+        la.ix = ix;
+        la.iy = iy;
+        la.sid = sid;
+        la.mark = mark;
+        la.flag = flag;
+        la.ind = ind;
+        la.count = N;
+        la.re_lo = h->re_lo;
+        la.im_lo = h->im_lo;
+        la.side = side;
+        eval_level(shift_table(h), la, 0, h->st);
+        h->stats.squares_evaluated += N;
+        h->stats.projected_solves += 8 * N;
+        const int nbk = cdiv_up(std::max<int64_t>(N, 1), 1024);
+        int64_t* bsum = h->arena.get<int64_t>("bsum", nbk + 1);
+        int64_t* tot = h->arena.get<int64_t>("tot", 1);
+        const int64_t cnt = count_marked(mark, N, bsum, tot, h->arena.host_i64(), h->st);
+        const bool last = (k == h->K);
+        if (!last) {
+            if (4 * cnt > h->opt.max_squares)
+                return fail(h, SIM_ERR_LIMIT, "level " + std::to_string(k + 1) + " would hold " +
+                                                  std::to_string(4 * cnt) + " squares (> max_squares)");
+            int64_t* nix = h->arena.get<int64_t>(b + "ix", 4 * cnt);
+            int64_t* niy = h->arena.get<int64_t>(b + "iy", 4 * cnt);
+            int* nsid = h->arena.get<int>(b + "sid", 4 * cnt);
+            emit_marked(mark, flag, ix, iy, sid, N, bsum, 0, nix, niy, nsid, nullptr, h->st);
+            h->cur = 1 - h->cur;
+            h->nsq = 4 * cnt;
+        } else {
+            int64_t* fix = h->arena.get<int64_t>("F_ix", cnt);
+            int64_t* fiy = h->arena.get<int64_t>("F_iy", cnt);
+            int* fsid = h->arena.get<int>("F_sid", cnt);
+            uint8_t* ffl = h->arena.get<uint8_t>("F_flag", cnt);
+            emit_marked(mark, flag, ix, iy, sid, N, bsum, 1, fix, fiy, fsid, ffl, h->st);
+            h->nfinal = cnt;
+            h->s_final = side;
+            h->state = ST_LEVELS_DONE;
+        }
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        h->stats.t_levels_ms += tl.ms();
+        h->stats.levels_done = k;
+        h->level = k + 1;
+        if (n_marked) *n_marked = cnt;
+        if (done) *done = last ? 1 : 0;
+        return SIM_OK;
+    });
+}
+
+sim_status sim_eigenvalues(sim_handle h, double* out, int64_t capacity, int64_t* count) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (h->state < ST_LEVELS_DONE) return fail(h, SIM_ERR_BAD_STATE, "levels not finished");
+        if (h->state == ST_LEVELS_DONE) {
+            Timer tm(h->st);
+            const int64_t N = h->nfinal;
+            h->eig.clear();
+            h->cl_shift.clear();
+            h->cl_size.clear();
+            h->cl_flag.clear();
+            h->cl_radius.clear();
+            if (N > 0) {
+                const int64_t nx = h->cols << (h->K - 1), ny = h->rows << (h->K - 1);
+                MergeResult R = merge_final(h->arena.get<int64_t>("F_ix", N), h->arena.get<int64_t>("F_iy", N),
+                                            h->arena.get<int>("F_sid", N), h->arena.get<uint8_t>("F_flag", N), N, nx,
+                                            ny, h->re_lo, h->re_hi, h->im_lo, h->im_hi, h->s_final,
+                                            h->opt.merge_radius, h->arena, h->st);
+                std::vector<double2> est(R.C);
+                std::vector<int> size(R.C), nfl(R.C), shift(R.C), rank(R.C);
+                std::vector<double> rad(R.C);
+                SIM_CUDA(cudaMemcpyAsync(est.data(), R.est, sizeof(double2) * R.C, cudaMemcpyDeviceToHost, h->st));
+                SIM_CUDA(cudaMemcpyAsync(size.data(), R.size, sizeof(int) * R.C, cudaMemcpyDeviceToHost, h->st));
+                SIM_CUDA(cudaMemcpyAsync(nfl.data(), R.nflag, sizeof(int) * R.C, cudaMemcpyDeviceToHost, h->st));
+                SIM_CUDA(cudaMemcpyAsync(shift.data(), R.shift, sizeof(int) * R.C, cudaMemcpyDeviceToHost, h->st));
+                SIM_CUDA(cudaMemcpyAsync(rank.data(), R.rank, sizeof(int) * R.C, cudaMemcpyDeviceToHost, h->st));
+                SIM_CUDA(cudaMemcpyAsync(rad.data(), R.radius, sizeof(double) * R.C, cudaMemcpyDeviceToHost, h->st));
+                SIM_CUDA(cudaStreamSynchronize(h->st));
+                h->eig.assign(R.inside, make_double2(0, 0));
+                h->cl_shift.assign(R.inside, 0);
+                h->cl_size.assign(R.inside, 0);
+                h->cl_flag.assign(R.inside, 0);
+                h->cl_radius.assign(R.inside, 0.0);
+                int64_t unres = 0;
+                for (int c = 0; c < R.C; ++c) {
+                    if (rank[c] < 0) continue;
+                    h->eig[rank[c]] = est[c];
+                    h->cl_shift[rank[c]] = shift[c];
+                    h->cl_size[rank[c]] = size[c];
+                    h->cl_flag[rank[c]] = nfl[c];
+                    h->cl_radius[rank[c]] = rad[c];
+                }
+                std::vector<uint8_t> ff(N);
+                SIM_CUDA(cudaMemcpy(ff.data(), h->arena.get<uint8_t>("F_flag", N), N, cudaMemcpyDeviceToHost));
+                for (auto v : ff) unres += v;
+                h->stats.unresolvable_final = unres;
+            }
+            h->stats.final_squares = N;
+            h->stats.clusters = (int64_t)h->eig.size();
+            h->stats.t_merge_ms += tm.ms();
+            h->state = ST_EIGS;
+        }
+        const int64_t C = (int64_t)h->eig.size();
+        if (count) *count = C;
+        if (capacity == 0) return SIM_OK;
+        if (capacity < C || !out) return fail(h, SIM_ERR_CAPACITY, "output capacity too small");
+        std::memcpy(out, h->eig.data(), sizeof(double2) * C);
+        return SIM_OK;
+    });
+}
+
+sim_status sim_multiplicity(sim_handle h, int32_t* out, int64_t capacity, int64_t* count) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (h->state != ST_EIGS) return fail(h, SIM_ERR_BAD_STATE, "call sim_eigenvalues first");
+        const int64_t C = (int64_t)h->eig.size();
+        if (h->mult.size() != (size_t)C) {
+            Timer tm(h->st);
+            MultInput mi;
+            mi.P = &h->P;
+            mi.opt = &h->opt;
+            mi.st = h->st;
+            mi.arena = &h->arena;
+            mi.d_sigma = h->d_sigma;
+            mi.d_fptrs = h->d_fptrs;
+            mi.est = h->eig;
+            mi.shift = h->cl_shift;
+            mi.radius = h->cl_radius;
+            mi.inner = &h->inner;
+            bool ok = true;
+            h->mult = multiplicities(mi, ok);
+            h->stats.t_mult_ms += tm.ms();
+            sync_stats(h);
+            if (!ok) return fail(h, SIM_ERR_NOT_CONVERGED, "an inner shifted solve did not converge");
+        }
+        if (count) *count = C;
+        if (capacity == 0) return SIM_OK;
+        if (capacity < C || !out) return fail(h, SIM_ERR_CAPACITY, "output capacity too small");
+        for (int64_t c = 0; c < C; ++c) out[c] = h->mult[c];
+        return SIM_OK;
+    });
+}
+
+sim_status sim_stats(sim_handle h, sim_stats_t* out, size_t size) {
+    if (!h || !out) return fail(h, SIM_ERR_INVALID_ARG, "NULL argument");
+    sync_stats(h);
+    std::memcpy(out, &h->stats, std::min(size, sizeof(sim_stats_t)));
+    return SIM_OK;
+}
+
+const char* sim_last_error(sim_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void sim_destroy(sim_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    delete h;
+}
+
+sim_status sim_shift_count(sim_handle h, int32_t* count) {
+    if (!h || !count) return fail(h, SIM_ERR_INVALID_ARG, "NULL argument");
+    *count = h->S;
+    return SIM_OK;
+}
+
+sim_status sim_get_shift(sim_handle h, int32_t s, double* sigma, double* H_host, double* beta, int32_t* m_eff) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (s < 0 || s >= h->S) return fail(h, SIM_ERR_INVALID_ARG, "shift index out of range");
+        const int m = h->opt.m;
+        if (sigma) {
+            sigma[0] = h->h_sigma[s].x;
+            sigma[1] = h->h_sigma[s].y;
+        }
+        if (H_host)
+            SIM_CUDA(cudaMemcpy(H_host, h->d_H + (size_t)s * (m + 1) * m, sizeof(double2) * (m + 1) * m,
+                                cudaMemcpyDeviceToHost));
+        if (beta) SIM_CUDA(cudaMemcpy(beta, h->d_beta + s, sizeof(double), cudaMemcpyDeviceToHost));
+        if (m_eff) SIM_CUDA(cudaMemcpy(m_eff, h->d_meff + s, sizeof(int), cudaMemcpyDeviceToHost));
+        return SIM_OK;
+    });
+}
+
+sim_status sim_eval_squares(const double* H, int32_t m, int32_t m_eff, double beta, double sig_re, double sig_im,
+                            const double* centers, const double* sides, int64_t count, int32_t residual_scale,
+                            double* indicator, double* rho, void* stream) {
+    return guarded(nullptr, [&]() -> sim_status {
+        if (!H || !centers || !sides || !indicator || !rho || count < 0 || m < 1 || m_eff < 1 || m_eff > m ||
+            eval_smem_bytes(m) > 220 * 1024)
+            return fail(nullptr, SIM_ERR_INVALID_ARG, "sim_eval_squares: bad argument (m <= 52)");
+        eval_explicit((const double2*)H, m, m_eff, beta, make_double2(sig_re, sig_im), (const double2*)centers, sides,
+                      count, residual_scale, indicator, rho, (cudaStream_t)stream);
+        SIM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        return SIM_OK;
+    });
+}
+
+sim_status sim_apply_shifted(sim_handle h, double sig_re, double sig_im, const double* x, double* y) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (!x || !y) return fail(h, SIM_ERR_INVALID_ARG, "NULL vector");
+        const int sc = h->cap - 1;
+        const double2 sg = make_double2(sig_re, sig_im);
+        SIM_CUDA(cudaMemcpyAsync(h->d_sigma + sc, &sg, sizeof(double2), cudaMemcpyHostToDevice, h->st));
+        JobSpace js = make_jobspace(h, 1, "cmp_");
+        SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
+        const int zero = 0;
+        SIM_CUDA(cudaMemcpyAsync(js.d_active, &zero, sizeof(int), cudaMemcpyHostToDevice, h->st));
+        SIM_CUDA(cudaMemcpyAsync(js.vec + (size_t)VS_X * js.n, x, sizeof(double2) * js.n, cudaMemcpyDeviceToDevice, h->st));
+        spmv_shifted_jobs(h->P, js, 1, nullptr, VS_X, VS_W, h->d_sigma, h->st);
+        SIM_CUDA(cudaMemcpyAsync(y, js.vec + (size_t)VS_W * js.n, sizeof(double2) * js.n, cudaMemcpyDeviceToDevice, h->st));
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        return SIM_OK;
+    });
+}
+
+sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const double* r, double* x, int32_t* iters,
+                             double* relres) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (!r || !x) return fail(h, SIM_ERR_INVALID_ARG, "NULL vector");
+        const int sc = h->cap - 1;
+        const double2 sg = make_double2(sig_re, sig_im);
+        h->h_sigma[sc] = sg;
+        SIM_CUDA(cudaMemcpyAsync(h->d_sigma + sc, &sg, sizeof(double2), cudaMemcpyHostToDevice, h->st));
+        factor_storage(h, sc);
+        int* d_list = h->arena.get<int>("cmp_list", 1);
+        SIM_CUDA(cudaMemcpyAsync(d_list, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
+        factor_shifts(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st);
+        JobSpace js = make_jobspace(h, 1, "cmp_");
+        SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
+        SIM_CUDA(cudaMemcpyAsync(js.vec + (size_t)VS_RHS * js.n, r, sizeof(double2) * js.n, cudaMemcpyDeviceToDevice,
+                                 h->st));
+        InnerStats is;
+        bool ok = inner_solve(h->P, h->opt, js, {0}, h->d_sigma, h->d_fptrs, h->st, is);
+        SIM_CUDA(cudaMemcpyAsync(x, js.vec + (size_t)VS_X * js.n, sizeof(double2) * js.n, cudaMemcpyDeviceToDevice, h->st));
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        if (iters) *iters = (int32_t)is.iters;
+        if (relres) *relres = is.worst;
+        if (!ok) return fail(h, SIM_ERR_NOT_CONVERGED, "shifted solve did not converge");
+        return SIM_OK;
+    });
+}
+
+sim_status sim_random_vectors(uint64_t seed, int64_t n, int32_t k, int32_t first, double* out, void* stream) {
+    return guarded(nullptr, [&]() -> sim_status {
+        if (!out || n < 0 || k < 0 || first < 0) return fail(nullptr, SIM_ERR_INVALID_ARG, "bad argument");
+        random_vectors(seed, n, k, first, (double2*)out, n, (cudaStream_t)stream);
+        SIM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        return SIM_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+closed forms and exact inertia counts."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def simlib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2006_16117_gb300 as sim
+
+    return sim
+
+
+def _csr_arrays(M):
+    return (M.indptr, M.indices, M.data)
+
+
+def _pencil_small():
+    from workloads import cd2d_csr
+
+    A = cd2d_csr(12, (1.0, 0.5))
+    bd = np.random.default_rng(3).uniform(1.0, 2.0, A.n)
+    return A, bd
+
+
+# ---------------------------------------------------------------------------
+def test_random_vectors_match_oracle_philox(simlib):
+    from oracle.philox import random_vectors
+
+    for seed, n, k, first in ((0x5EED, 1000, 3, 0), (7, 1537, 2, 5)):
+        g = simlib.random_vectors(seed, n, k, first).cpu().numpy()
+        ref = random_vectors(seed, n, k, first).T
+        assert np.max(np.abs(g - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_apply_shifted_matches_scipy(simlib):
+    from workloads import diag_csr
+
+    A, bd = _pencil_small()
+    B = diag_csr(bd)
+    s = simlib.Sim(A, B)
+    x = np.random.default_rng(1).standard_normal(A.n) + 1j * np.random.default_rng(2).standard_normal(A.n)
+    sigma = 850.0 + 0.2j
+    y = s.apply_shifted(sigma, torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = (A.to_scipy() - sigma * B.to_scipy()) @ x
+    assert np.max(np.abs(y - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shifted_solve_matches_sparse_lu(simlib, precision):
+    from workloads import block_diag_csr, jordan_csr, diag_csr
+
+    A0, bd = _pencil_small()
+    A = block_diag_csr(A0, jordan_csr([900.0 + 0.35j, 1300.0 + 0.35j], 4, 1e-7))  # ragged last block
+    B = diag_csr(np.concatenate([bd, np.ones(8)]))
+    s = simlib.Sim(A, B, simlib.sim_default_options(precision=precision))
+    r = np.random.default_rng(4).standard_normal(A.n) + 0.5j
+    sigma = 905.3 + 0.2j
+    x, iters, rel = s.shifted_solve(sigma, torch.from_numpy(r).cuda())
+    x = x.cpu().numpy()
+    K = (A.to_scipy() - sigma * B.to_scipy()).tocsc()
+    ref = spla.splu(K).solve(r)
+    assert rel <= 1e-12
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert iters >= 1
+
+
+def test_eval_squares_with_oracle_krylov_space(simlib):
+    from oracle import simm as S
+    from workloads import config_small
+
+    w = config_small()
+    ks = S.cayley_arnoldi(w.A.to_scipy(), sp.identity(w.A.n, format="csr", dtype=complex), 3990.0 + 0.2j, w.f, 50)
+    rng = np.random.default_rng(9)
+    centers = rng.uniform(3950, 4030, 300) + 1j * rng.uniform(-0.3, 0.7, 300)
+    sides = 2.0 ** -rng.integers(0, 20, 300)
+    for scale, name in ((0, "solution"), (1, "beta")):
+        ind, rho = simlib.eval_squares(ks.H, ks.m_eff, ks.beta, ks.sigma, centers, sides, scale)
+        ind_o, rho_o = S.evaluate_squares(ks, centers, sides, name)
+        ok = np.isfinite(ind_o)
+        assert np.all(np.abs(ind[ok] - ind_o[ok]) <= 1e-9 * np.maximum(1.0, ind_o[ok]))
+        # the resolvability decision (Def. 3.1, ε = 1e-8) agrees wherever it is not a near-tie
+        clear = np.abs(np.log10(np.maximum(rho_o, 1e-300)) + 8.0) > 0.01
+        assert np.array_equal((rho <= 1e-8)[clear], (rho_o <= 1e-8)[clear])
+        big = rho_o > 1e-13
+        assert np.all(np.abs(rho[big] - rho_o[big]) <= 1e-6 * rho_o[big])
+
+
+def test_krylov_space_matches_oracle(simlib):
+    from oracle import simm as S
+    from workloads import config_small
+
+    w = config_small()
+    s = simlib.Sim(w.A, None)
+    s.set_region(w.region, w.f)
+    sigma, H, beta, meff = s.get_shift(0)
+    ks = S.cayley_arnoldi(w.A.to_scipy(), sp.identity(w.A.n, format="csr", dtype=complex), sigma, w.f, 50)
+    assert meff == ks.m_eff == 50
+    assert abs(beta - ks.beta) <= 1e-11 * ks.beta
+    # leading columns agree to rounding; the subdiagonal is real and positive
+    assert np.max(np.abs(H[:12, :10] - ks.H[:12, :10])) <= 1e-8 * np.max(np.abs(ks.H))
+    assert np.all(np.diag(H, -1).real > 0)
+    # indicators of squares near σ computed from either space agree
+    centers = sigma + np.linspace(-15, 15, 61) + 0.05j
+    i_gpu, _ = S.evaluate_squares(S.KrylovSpace(sigma, H, beta, meff), centers, np.full(61, 0.5))
+    i_ora, _ = S.evaluate_squares(ks, centers, np.full(61, 0.5))
+    assert np.all(np.abs(i_gpu - i_ora) <= 1e-6 * np.maximum(1.0, i_ora))
+
+
+@pytest.fixture(scope="module")
+def small_oracle():
+    from oracle import simm as S
+    from workloads import config_small
+
+    w = config_small()
+    return w, S.sim_m(w.A.to_scipy(), None, w.region, w.f, S.Options(**w.options))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_simm_small_convection_diffusion(simlib, small_oracle, precision):
+    w, ref = small_oracle
+    opt = simlib.sim_default_options(precision=precision, **w.options)
+    eig, mult, st = simlib.run(w.A, None, w.region, w.f, opt)
+    assert eig.size == ref.eigenvalues.size == w.expected_count == 50
+    assert np.max(np.abs(eig - ref.eigenvalues)) <= 1e-6
+    assert np.max(np.abs(np.sort(eig.real) - np.sort(w.reference_eigs.real))) <= 1e-6
+    assert np.array_equal(mult, ref.multiplicities)
+    assert st["unresolvable_final"] == 0
+    assert st["max_inner_residual"] <= 1e-12
+
+
+def test_simm_jordan_multiplicity(simlib):
+    from oracle import simm as S
+    from workloads import config_jordan_small
+
+    w = config_jordan_small()
+    ref = S.sim_m(w.A.to_scipy(), None, w.region, w.f, S.Options(**w.options))
+    eig, mult, _ = simlib.run(w.A, None, w.region, w.f, simlib.sim_default_options(**w.options))
+    assert eig.size == ref.eigenvalues.size == w.reference_eigs.size
+    assert np.max(np.abs(eig - ref.eigenvalues)) <= 1e-6
+    assert np.array_equal(mult, ref.multiplicities)
+    assert np.array_equal(mult, w.reference_mult)
+
+
+def test_simm_generalized_pencil_vs_dense_qz(simlib):
+    import scipy.linalg as sla
+
+    from workloads import cd2d_csr, diag_csr
+
+    N = 15
+    A0 = cd2d_csr(N, (1.0, 0.5))
+    bd = np.random.default_rng(11).uniform(1.0, 2.0, A0.n)
+    lam = sla.eigvals(A0.to_dense(), np.diag(bd))
+    lr = np.sort(lam.real)
+    lo, hi = 0.5 * (lr[99] + lr[100]), 0.5 * (lr[119] + lr[120])
+    f = np.random.default_rng(12).standard_normal(A0.n) + 0j
+    eig, mult, _ = simlib.run(A0, diag_csr(bd), (lo, hi, -0.3, 0.7), f)
+    assert eig.size == 20
+    assert np.max(np.abs(np.sort(eig.real) - np.sort(lam[(lam.real > lo) & (lam.real < hi)].real))) <= 1e-6
+    assert np.all(mult == 1)
+
+
+def test_simm_laplacian_degenerate_multiplicity(simlib):
+    from oracle import simm as S
+    from workloads import cd2d_csr
+
+    N = 8
+    A = cd2d_csr(N, (0.0, 0.0))
+    ev = np.sort(np.linalg.eigvalsh(A.to_dense().real))
+    h = 1.0 / (N + 1)
+    c = 4.0 / h**2
+    uniq = np.unique(np.round(ev, 6))
+    j = int(np.argmin(np.abs(uniq - c)))
+    lo, hi = 0.5 * (uniq[j - 3] + uniq[j - 2]), 0.5 * (uniq[j + 2] + uniq[j + 3])
+    f = np.random.default_rng(13).standard_normal(A.n) + 0j
+    ref = S.sim_m(A.to_scipy(), None, (lo, hi, -0.4, 0.6), f, S.Options())
+    eig, mult, _ = simlib.run(A, None, (lo, hi, -0.4, 0.6), f)
+    assert np.max(np.abs(eig - ref.eigenvalues)) <= 1e-6
+    assert np.array_equal(mult, ref.multiplicities)
+    assert mult.max() == N  # the eigenvalue 4/h^2 has multiplicity N
+
+
+def test_empty_region_and_state_errors(simlib):
+    from workloads import cd2d_csr, complex_gaussian
+
+    A = cd2d_csr(10, (1.0, 0.5))
+    s = simlib.Sim(A, None)
+    with pytest.raises(simlib.SimError) as e:
+        s.solve_level()
+    assert e.value.status == 2  # SIM_ERR_BAD_STATE
+    s.set_region((-50.0, -10.0, -1.0, 1.0), complex_gaussian(A.n, 0))  # left of the spectrum
+    s.solve_all_levels()
+    assert s.eigenvalues().size == 0
+    assert s.multiplicity().size == 0
+    with pytest.raises(simlib.SimError) as e:
+        s.solve_level()
+    assert e.value.status == 2
+
+
+def test_invalid_csr_is_rejected(simlib):
+    bad = (np.array([0, 2, 3], np.int32), np.array([1, 0, 1], np.int32), np.ones(3, complex))  # unsorted row 0
+    with pytest.raises(simlib.SimError) as e:
+        simlib.Sim(bad, None)
+    assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# the benchmark configuration at full size: n = 40,064, B diagonal, Jordan blocks
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def pencil_run(simlib):
+    from workloads import config_pencil
+
+    w = config_pencil()
+    opt = simlib.sim_default_options(precision="mixed", **w.options)
+    eig, mult, st = simlib.run(w.A, w.B, w.region, w.f, opt)
+    return w, eig, mult, st
+
+
+def test_pencil_counts_and_multiplicities(pencil_run):
+    from workloads.configs import jordan_eigs
+
+    w, eig, mult, st = pencil_run
+    assert int(mult.sum()) == w.expected_count == 564
+    je = jordan_eigs(w.region)
+    jd = np.abs(eig[:, None] - je[None, :])
+    is_j = jd.min(axis=1) < 1e-3
+    assert is_j.sum() == 16
+    assert np.all(mult[is_j] == 4)
+    assert np.all(mult[~is_j] == 1)
+    assert np.max(jd.min(axis=0)) <= 1e-6
+    assert np.max(np.abs(eig[~is_j].imag)) <= 1e-6  # the convection-diffusion pencil is real
+
+
+def test_pencil_sampled_eigenvalues_by_inertia(pencil_run):
+    from oracle.inertia import count_below
+    from workloads.configs import pencil_parts
+
+    w, eig, mult, st = pencil_run
+    _, bd = pencil_parts(200, 1)
+    real = np.sort(eig[np.abs(eig.imag) < 1e-3].real)
+    rng = np.random.default_rng(0)
+    for x in rng.choice(real, 6, replace=False):
+        # exactly one eigenvalue of the pencil within 2e-6 of each sampled estimate
+        assert count_below(200, (1.0, 0.5), bd, x + 2e-6) - count_below(200, (1.0, 0.5), bd, x - 2e-6) == 1
