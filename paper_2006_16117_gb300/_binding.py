@@ -133,7 +133,8 @@ class _HostCsr:
         if hasattr(M, "indptr"):
             indptr, indices, data, n = M.indptr, M.indices, M.data, M.shape[0] if hasattr(M, "shape") else M.n
         else:
-            indptr, indices, data, n = M
+            indptr, indices, data = M
+            n = len(indptr) - 1
         self.indptr = np.ascontiguousarray(indptr, dtype=np.int32)
         self.indices = np.ascontiguousarray(indices, dtype=np.int32)
         self.data = np.ascontiguousarray(data, dtype=np.complex128)

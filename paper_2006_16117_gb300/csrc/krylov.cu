@@ -697,9 +697,15 @@ __global__ void k_gm_check(JobSpace js, int nactive, const double2* pin, int nch
     int* is = js.istat + (size_t)job * IS_N;
     const double r = sqrt(s);
     const double rel = sc[SC_RNORM0] > 0 ? r / sc[SC_RNORM0] : 0.0;
+    const double prev = sc[SC_GAMMA] > 0 && sc[SC_RNORM0] > 0 ? sc[SC_GAMMA] / sc[SC_RNORM0] : INFINITY;
     sc[SC_WORST] = rel;
-    if (rel <= tol) is[IS_DONE] = 1;
-    else if (is[IS_ITERS] >= max_iter) is[IS_DONE] = -1;  // not converged
+    if (rel <= tol) {
+        is[IS_DONE] = 1;
+    } else if (is[IS_ITERS] >= max_iter || rel > 0.5 * prev) {
+        // iteration cap, or a restart cycle that did not halve the residual
+        // (stagnation at the rounding floor): accept within 100 tol, else fail
+        is[IS_DONE] = rel <= 100.0 * tol ? 1 : -1;
+    }
 }
 
 namespace {
