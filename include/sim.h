@@ -222,6 +222,19 @@ sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const d
 sim_status sim_random_vectors(uint64_t seed, int64_t n, int32_t k, int32_t first, double* out,
                               void* stream);
 
+/* ---- Instrumentation ------------------------------------------------------
+ * Not part of the method: counters used by the benchmark.
+ * sim_kernel_timing(1) resets and turns on per-kernel CUDA-event timing of the
+ * library's main kernels ("block_solve", "factor", "gram_schmidt",
+ * "eval_level"); 0 turns it off.  Process-wide, not thread-safe.
+ * sim_kernel_stats fills the accumulated device time (ms), algorithmic bytes
+ * and flops and launch count of one of them; returns 0 if it never ran.
+ * sim_launch_count returns the number of kernel launches the library has made
+ * in this process. */
+void sim_kernel_timing(int32_t enable);
+int32_t sim_kernel_stats(const char* name, double* ms, double* bytes, double* flops, int64_t* launches);
+int64_t sim_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

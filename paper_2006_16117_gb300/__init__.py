@@ -19,6 +19,9 @@ from ._binding import (  # noqa: F401
     lib,
     library_path,
     random_vectors,
+    kernel_timing,
+    kernel_stats,
+    launch_count,
     sim_default_options,
     run,
 )

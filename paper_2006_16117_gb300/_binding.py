@@ -62,6 +62,7 @@ EXPORTS = [
     "sim_default_options", "sim_create", "sim_set_region", "sim_solve_level", "sim_eigenvalues",
     "sim_multiplicity", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
     "sim_eval_squares", "sim_apply_shifted", "sim_shifted_solve", "sim_random_vectors",
+    "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count",
 ]
 
 
@@ -92,6 +93,12 @@ def lib():
     L.sim_apply_shifted.argtypes = [vp, dbl, dbl, vp, vp]
     L.sim_shifted_solve.argtypes = [vp, dbl, dbl, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
     L.sim_random_vectors.argtypes = [u64, i64, i32, i32, vp, vp]
+    L.sim_kernel_timing.argtypes = [i32]
+    L.sim_kernel_timing.restype = None
+    L.sim_kernel_stats.argtypes = [C.c_char_p, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl), C.POINTER(i64)]
+    L.sim_kernel_stats.restype = i32
+    L.sim_launch_count.argtypes = []
+    L.sim_launch_count.restype = i64
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is C.c_int:  # default restype: sim_status
@@ -297,6 +304,21 @@ def eval_squares(H, m_eff, beta, sigma, centers, sides, residual_scale=0, stream
                                 int(residual_scale), ind.data_ptr(), rho.data_ptr(), _stream_ptr(stream))
     _check(st, None)
     return ind.cpu().numpy(), rho.cpu().numpy()
+
+
+def kernel_timing(enable: bool):
+    lib().sim_kernel_timing(1 if enable else 0)
+
+
+def kernel_stats(name: str):
+    ms, by, fl, ln = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+    if not lib().sim_kernel_stats(name.encode(), C.byref(ms), C.byref(by), C.byref(fl), C.byref(ln)):
+        return None
+    return {"ms": ms.value, "bytes": by.value, "flops": fl.value, "launches": ln.value}
+
+
+def launch_count() -> int:
+    return int(lib().sim_launch_count())
 
 
 def random_vectors(seed, n, k, first=0, stream=None):

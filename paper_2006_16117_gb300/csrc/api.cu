@@ -812,6 +812,18 @@ sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const d
     });
 }
 
+void sim_kernel_timing(int32_t enable) {
+    kprof_reset();
+    kprof_enable(enable != 0);
+}
+
+int32_t sim_kernel_stats(const char* name, double* ms, double* bytes, double* flops, int64_t* launches) {
+    if (!name) return 0;
+    return kprof_query(name, ms, bytes, flops, launches) ? 1 : 0;
+}
+
+int64_t sim_launch_count(void) { return launch_counter(); }
+
 sim_status sim_random_vectors(uint64_t seed, int64_t n, int32_t k, int32_t first, double* out, void* stream) {
     return guarded(nullptr, [&]() -> sim_status {
         if (!out || n < 0 || k < 0 || first < 0) return fail(nullptr, SIM_ERR_INVALID_ARG, "bad argument");

@@ -104,7 +104,24 @@ struct CudaError {
             throw ::sim::CudaError{e_, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
     } while (0)
 
-#define SIM_LAUNCH_CHECK() SIM_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by this check, which also
+// counts launches (sim_kernel_stats reports the count)
+int64_t& launch_counter();
+#define SIM_LAUNCH_CHECK()                 \
+    do {                                   \
+        ++::sim::launch_counter();         \
+        SIM_CUDA(cudaGetLastError());      \
+    } while (0)
+
+// Optional per-kernel timing with CUDA events on the launching stream (off by
+// default; sim_options.kernel_timing turns it on).  kprof_end adds the
+// algorithmic bytes and flops of the launch.
+void kprof_begin(const char* name, cudaStream_t st);
+void kprof_end(const char* name, cudaStream_t st, double bytes, double flops);
+bool kprof_enabled();
+void kprof_enable(bool on);
+void kprof_reset();
+bool kprof_query(const char* name, double* ms, double* bytes, double* flops, int64_t* launches);
 
 inline int cdiv_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

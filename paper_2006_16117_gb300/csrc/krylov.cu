@@ -190,14 +190,21 @@ void factor_shifts(const Pencil& P, int precision, const int* d_shift_list, int 
     if (!d_err) SIM_CUDA(cudaMalloc(&d_err, sizeof(int)));
     SIM_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     size_t sm = factor_smem(P.T, precision);
+    kprof_begin("factor", st);
     if (precision == SIM_FP64) {
         SIM_CUDA(cudaFuncSetAttribute(k_factor<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_factor<double2><<<count, FACTOR_THREADS, sm, st>>>(P, d_shift_list, d_sigma, d_factor_ptrs, d_err);
+        SIM_LAUNCH_CHECK();
     } else {
         SIM_CUDA(cudaFuncSetAttribute(k_factor<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_factor<float2><<<count, FACTOR_THREADS, sm, st>>>(P, d_shift_list, d_sigma, d_factor_ptrs, d_err);
+        SIM_LAUNCH_CHECK();
     }
-    SIM_LAUNCH_CHECK();
+    {
+        const double cs = precision == SIM_FP64 ? sizeof(double2) : sizeof(float2);
+        const double TT = (double)P.T * P.T;
+        kprof_end("factor", st, count * (2.0 * P.nb * TT * cs), count * 8.0 * P.nb * TT * P.T);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -288,14 +295,18 @@ void block_solve(const Pencil& P, int precision, const JobSpace& js, int nactive
     if (nactive <= 0) return;
     size_t cs = precision == SIM_FP64 ? sizeof(double2) : sizeof(float2);
     size_t sm = 3 * P.T * cs;
+    const double TT = (double)P.T * P.T, blocks = 2.0 * P.nb - 1.0;
+    kprof_begin("block_solve", st);
     if (precision == SIM_FP64) {
         SIM_CUDA(cudaFuncSetAttribute(k_block_solve<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_block_solve<double2><<<nactive, SOLVE_THREADS, sm, st>>>(P, js, in_slot, out_slot, d_sigma, d_factor_ptrs);
+        SIM_LAUNCH_CHECK();
     } else {
         SIM_CUDA(cudaFuncSetAttribute(k_block_solve<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_block_solve<float2><<<nactive, SOLVE_THREADS, sm, st>>>(P, js, in_slot, out_slot, d_sigma, d_factor_ptrs);
+        SIM_LAUNCH_CHECK();
     }
-    SIM_LAUNCH_CHECK();
+    kprof_end("block_solve", st, nactive * (blocks * TT * cs + 4.0 * P.n * sizeof(double2)), nactive * 8.0 * blocks * TT);
 }
 
 // ---------------------------------------------------------------------------
@@ -549,6 +560,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_finish(GSArgs a) {
 
 // one CGS2 step on the active jobs: partial buffers A = partial, B = partial + half
 static void gs_run(GSArgs a, double2* partial, size_t half, int nactive, cudaStream_t st) {
+    kprof_begin("gram_schmidt", st);
     dim3 grid(a.nchunk, nactive);
     const int nw = GS_THREADS / 32;
     size_t sm_dots = (size_t)std::max(a.cnt, 1) * nw * sizeof(double2) + 64;
@@ -569,6 +581,7 @@ static void gs_run(GSArgs a, double2* partial, size_t half, int nactive, cudaStr
     a.pin = A;
     k_gs_finish<<<grid, GS_THREADS, 0, st>>>(a);
     SIM_LAUNCH_CHECK();
+    kprof_end("gram_schmidt", st, nactive * (4.0 * a.cnt + 6.0) * a.n * sizeof(double2), nactive * 32.0 * a.cnt * a.n);
 }
 
 // ---------------------------------------------------------------------------
@@ -777,6 +790,7 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
     std::vector<int> cyc = jobs;  // jobs that start a cycle
     upload_active(js, cyc, st);
     k_zero_slot<<<rows_grid((int)cyc.size()), 256, 0, st>>>(js, VS_X);
+    SIM_LAUNCH_CHECK();
     k_copy_slot<<<rows_grid((int)cyc.size()), 256, 0, st>>>(js, VS_RHS, VS_R);
     SIM_LAUNCH_CHECK();
     bool first = true;
@@ -785,6 +799,7 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
         const int nc = (int)cyc.size();
         upload_active(js, cyc, st);
         k_copy_slot<<<rows_grid(nc), 256, 0, st>>>(js, VS_R, VS_Q0);
+        SIM_LAUNCH_CHECK();
         norm_and_scale(js, nc, js.vec + (size_t)VS_Q0 * js.n, js.vstride, js.g, k + 1, st);
         k_gm_cycle_init<<<cdiv_up(nc, 128), 128, 0, st>>>(js, nc, first ? 1 : 0, opt.inner_tol);
         SIM_LAUNCH_CHECK();
@@ -825,6 +840,7 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
         const int ni = (int)in_cycle.size();
         upload_active(js, in_cycle, st);
         k_gm_update_x<<<rows_grid(ni), 256, 0, st>>>(js);
+        SIM_LAUNCH_CHECK();
         k_spmv_jobs<<<rows_grid(ni), 256, 0, st>>>(P, js, VS_X, VS_R, VS_RHS, d_sigma);
         SIM_LAUNCH_CHECK();
         {
@@ -900,6 +916,7 @@ bool arnoldi(const Pencil& P, const sim_options& opt, JobSpace& js, const double
     bool ok = inner_solve(P, opt, js, all, d_sigma, d_factor_ptrs, st, stats);  // b = K^{-1} f
     upload_active(js, all, st);
     k_arnoldi_init<<<cdiv_up(J, 128), 128, 0, st>>>(js, J);
+    SIM_LAUNCH_CHECK();
     k_copy_to_V<<<rows_grid(J), 256, 0, st>>>(js, VS_X, 0);
     SIM_LAUNCH_CHECK();
     // beta = ||b||, v_1 = b / beta   (the norm lands in g[job*(k+1)] as scratch)

@@ -195,8 +195,10 @@ void eval_level(const ShiftTable& st, const LevelArgs& a, int mode, cudaStream_t
     const size_t sm = eval_smem_bytes(st.m);
     SIM_CUDA(cudaFuncSetAttribute(k_eval_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int grid = (int)std::min<int64_t>(a.count, 152 * 64);
+    kprof_begin("eval_level", stream);
     k_eval_level<<<grid, 256, sm, stream>>>(st, a, mode);
     SIM_LAUNCH_CHECK();
+    kprof_end("eval_level", stream, 0.0, a.count * 8.0 * 8.0 * st.m * st.m);
 }
 
 // explicit squares against one explicit Krylov space (component entry point)
@@ -324,6 +326,7 @@ int64_t count_marked(const uint8_t* mark, int64_t count, int64_t* d_bsum, int64_
     if (count <= 0) return 0;
     const int nb = cdiv_up(count, SCAN_T);
     k_count_marks<<<nb, SCAN_T, 0, st>>>(mark, count, d_bsum);
+    SIM_LAUNCH_CHECK();
     k_scan_bsums<<<1, SCAN_T, 0, st>>>(d_bsum, nb, d_total);
     SIM_LAUNCH_CHECK();
     SIM_CUDA(cudaMemcpyAsync(h_total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -553,14 +556,19 @@ MergeResult merge_final(const int64_t* d_ix, const int64_t* d_iy, const int* d_s
     SIM_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * cap, st));
     const int g = cdiv_up(N, 256);
     k_hash_insert<<<g, 256, 0, st>>>(d_ix, d_iy, N, ny, keys, vals, cap);
+    SIM_LAUNCH_CHECK();
     k_uf_init<<<g, 256, 0, st>>>(parent, N);
+    SIM_LAUNCH_CHECK();
     k_uf_neighbours<<<g, 256, 0, st>>>(d_ix, d_iy, N, nx, ny, keys, vals, cap, parent);
+    SIM_LAUNCH_CHECK();
     k_uf_flatten<<<g, 256, 0, st>>>(parent, N);
     SIM_LAUNCH_CHECK();
     for (int pass = 0; pass < 2; ++pass) {
         k_root_flags<<<g, 256, 0, st>>>(parent, N, isroot);
+        SIM_LAUNCH_CHECK();
         const int64_t C = count_marked(isroot, N, bsum, total, h_total, st);
         k_root_ids<<<nb, SCAN_T, 0, st>>>(isroot, N, bsum, cidr);
+        SIM_LAUNCH_CHECK();
         k_labels<<<g, 256, 0, st>>>(parent, cidr, N, label);
         SIM_LAUNCH_CHECK();
         R.C = (int)C;
@@ -575,7 +583,9 @@ MergeResult merge_final(const int64_t* d_ix, const int64_t* d_iy, const int* d_s
         if (pass == 1 || !(merge_radius > 0.0) || C < 2) break;
         auto* roc = arena.get<int>("m_roc", C);
         k_root_of_cluster<<<g, 256, 0, st>>>(cidr, N, roc);
+        SIM_LAUNCH_CHECK();
         k_join_close<<<cdiv_up(C, 128), 128, 0, st>>>(R.est, roc, (int)C, merge_radius, parent);
+        SIM_LAUNCH_CHECK();
         k_uf_flatten<<<g, 256, 0, st>>>(parent, N);
         SIM_LAUNCH_CHECK();
     }
