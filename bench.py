@@ -165,8 +165,7 @@ def traffic_record(kernel: str, precision: str):
 
 def cpu_baseline(w_full):
     """The oracle as it stands, on a bounded sample of the same workload: a
-    60-unit-wide slice of the region (about 17 eigenvalues plus one 4-fold
-    Jordan eigenvalue)."""
+    30-unit-wide slice of the region (about 9 eigenvalues)."""
     from oracle import simm as S
 
     re_lo, re_hi, im_lo, im_hi = w_full.region

@@ -219,6 +219,7 @@ bool build_shifts(sim_ctx* h, const std::vector<double2>& sig) {
     h->stats.t_factor_ms += tf.ms();
     Timer tk(h->st);
     JobSpace js = make_jobspace(h, J, "loc_");
+    js.h_jobshift = ids.data();
     SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
     dim3 grid(cdiv_up(h->P.n, 256), J);
     k_copy_start<<<grid, 256, 0, h->st>>>(js, J, h->d_f);
@@ -356,7 +357,8 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
         Pencil& P = h->P;
         P.n = n;
         P.nnz = (int64_t)ci.size();
-        P.T = (int)std::max<int64_t>(1, std::max(kl, ku));
+        P.T = (int)std::max<int64_t>(2, std::max(kl, ku));
+        P.T += P.T & 1;  // even: block rows stay 16-byte aligned in complex64
         P.nb = (int)((n + P.T - 1) / P.T);
         P.b_kind = hasB ? (bdiag ? 1 : 2) : 0;
         // couplings to the next block row, column-compressed per block
@@ -798,6 +800,7 @@ sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const d
         SIM_CUDA(cudaMemcpyAsync(d_list, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
         factor_shifts(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st);
         JobSpace js = make_jobspace(h, 1, "cmp_");
+        js.h_jobshift = &sc;
         SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
         SIM_CUDA(cudaMemcpyAsync(js.vec + (size_t)VS_RHS * js.n, r, sizeof(double2) * js.n, cudaMemcpyDeviceToDevice,
                                  h->st));

@@ -63,7 +63,7 @@ struct JobSpace {
     int pw = 0;                // partial width
     int* d_jobshift = nullptr; // [J] shift id of each slot
     int* d_active = nullptr;   // [J] active slot list
-    std::vector<int> h_jobshift;
+    const int* h_jobshift = nullptr;  // [J] the same ids in host memory (owned by the caller)
 };
 
 // vector slots inside vec

@@ -24,6 +24,7 @@
 
 #include "internal.h"
 #include "levels.h"
+#include "solve_cluster.h"
 
 namespace sim {
 
@@ -812,7 +813,9 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
         for (int i = 0; i < k && !act.empty(); ++i) {
             const int na = (int)act.size();
             upload_active(js, act, st);
-            block_solve(P, opt.precision, js, na, VS_Q0 + i, vs_Z(k) + i, d_sigma, d_factor_ptrs, st);
+            if (!js.h_jobshift ||
+                !block_solve_cluster(P, opt.precision, js, act, VS_Q0 + i, vs_Z(k) + i, d_sigma, d_factor_ptrs, st))
+                block_solve(P, opt.precision, js, na, VS_Q0 + i, vs_Z(k) + i, d_sigma, d_factor_ptrs, st);
             k_spmv_jobs<<<rows_grid(na), 256, 0, st>>>(P, js, vs_Z(k) + i, VS_Q0 + i + 1, -1, d_sigma);
             SIM_LAUNCH_CHECK();
             GSArgs a{};

@@ -250,6 +250,7 @@ std::vector<int> multiplicities(const MultInput& in, bool& ok) {
                 cl_ptr.push_back((int)cl_list.size());
             }
             const int Cp = (int)cl_id.size();
+            js.h_jobshift = jobshift.data();
             SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, jobshift.data(), sizeof(int) * J, cudaMemcpyHostToDevice, st));
             dim3 g1(cdiv_up(n, 256), J);
             k_mult_start<<<g1, 256, 0, st>>>(js, J, k, F);

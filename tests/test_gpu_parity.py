@@ -116,9 +116,9 @@ def test_eval_squares_with_oracle_krylov_space(simlib):
     # squares the space resolves (Def. 3.1) and that are not tiny: tight agreement
     ind, rho = simlib.eval_squares(ks.H, ks.m_eff, ks.beta, ks.sigma, centers, sides, 0)
     ind_o, rho_o = S.evaluate_squares(ks, centers, sides, "solution")
-    sel = (rho_o <= 1e-8) & (sides >= 1e-3)
-    assert sel.sum() > 10
-    assert np.all(np.abs(ind[sel] - ind_o[sel]) <= 1e-9 * np.maximum(1.0, ind_o[sel]) + 1e-7)
+    sel = (rho_o <= 1e-8) & (sides >= 1e-3) & (ind_o > 1e-2)
+    assert sel.sum() >= 5
+    assert np.all(np.abs(ind[sel] - ind_o[sel]) <= 1e-7 * ind_o[sel])
 
 
 def test_krylov_space_matches_oracle(simlib):
