@@ -217,6 +217,21 @@ sim_status sim_apply_shifted(sim_handle h, double sig_re, double sig_im, const d
 sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const double* r, double* x,
                              int32_t* iters, double* relres);
 
+/* y = (A - σB) x like sim_apply_shifted, for callers that must not allocate
+ * device memory: a process whose GPU memory is owned by another allocator (a
+ * framework's caching pool that reserved it), where a cudaMalloc would fail or
+ * fragment that pool, or a latency-critical loop that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree may cause.  The paper has no counterpart:
+ * this is a deployment variant of the sparse apply.  It stages x and y in one
+ * file-scope device array (n <= 262,144 complex128 per vector, about 8 MiB,
+ * held by every GPU that loads the library until exit) and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The array's device
+ * address is looked up on the first call made on each device (make that first
+ * call before any stream capture).  Calls share the array: each call fully
+ * overwrites what it reads, and calls that overlap on the GPU race.
+ * Errors: SIM_ERR_LIMIT when n exceeds 262,144; SIM_ERR_INVALID_ARG; SIM_ERR_CUDA. */
+sim_status sim_apply_shifted_noalloc(sim_handle h, double sig_re, double sig_im, const double* x, double* y);
+
 /* Philox4x64-10 complex Gaussian vectors: out[v*n + e] for v < k is element e
  * of random vector (first + v) with key (seed, 0x53494D4D); complex128. */
 sim_status sim_random_vectors(uint64_t seed, int64_t n, int32_t k, int32_t first, double* out,

@@ -62,7 +62,7 @@ EXPORTS = [
     "sim_default_options", "sim_create", "sim_set_region", "sim_solve_level", "sim_eigenvalues",
     "sim_multiplicity", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
     "sim_eval_squares", "sim_apply_shifted", "sim_shifted_solve", "sim_random_vectors",
-    "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count",
+    "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count", "sim_apply_shifted_noalloc",
 ]
 
 
@@ -91,6 +91,7 @@ def lib():
     L.sim_get_shift.argtypes = [vp, i32, vp, vp, vp, C.POINTER(i32)]
     L.sim_eval_squares.argtypes = [vp, i32, i32, dbl, dbl, dbl, vp, vp, i64, i32, vp, vp, vp]
     L.sim_apply_shifted.argtypes = [vp, dbl, dbl, vp, vp]
+    L.sim_apply_shifted_noalloc.argtypes = [vp, dbl, dbl, vp, vp]
     L.sim_shifted_solve.argtypes = [vp, dbl, dbl, vp, vp, C.POINTER(i32), C.POINTER(dbl)]
     L.sim_random_vectors.argtypes = [u64, i64, i32, i32, vp, vp]
     L.sim_kernel_timing.argtypes = [i32]

@@ -263,6 +263,27 @@ void sync_stats(sim_ctx* h) {
 
 }  // namespace
 
+// Accessors for sim_apply_shifted_noalloc (noalloc.cu).
+namespace sim {
+struct NoallocView {
+    const Pencil* P;
+    double2* d_sigma;
+    int scratch_slot;
+    cudaStream_t st;
+};
+bool noalloc_view(sim_handle h, NoallocView* v) {
+    if (!h || !h->d_sigma || h->cap < 1) return false;
+    v->P = &h->P;
+    v->d_sigma = h->d_sigma;
+    v->scratch_slot = h->cap - 1;
+    v->st = h->st;
+    return true;
+}
+void noalloc_fail(sim_handle h, const std::string& msg) {
+    if (h) h->err = msg;
+}
+}  // namespace sim
+
 // ---------------------------------------------------------------------------
 extern "C" {
 
