@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "factor_cluster.h"
 #include "levels.h"
 #include "mult.h"
 
@@ -215,7 +216,8 @@ bool build_shifts(sim_ctx* h, const std::vector<double2>& sig) {
     int* d_list = h->arena.get<int>("shift_list", J);
     SIM_CUDA(cudaMemcpyAsync(d_list, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
     Timer tf(h->st);
-    factor_shifts(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st);
+    if (!factor_shifts_cluster(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st))
+        factor_shifts(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st);
     h->stats.t_factor_ms += tf.ms();
     Timer tk(h->st);
     JobSpace js = make_jobspace(h, J, "loc_");
@@ -408,6 +410,19 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
                 }
             }
         }
+        // couplings to the previous block row
+        std::vector<int32_t> Lptr(n + 1, 0), Lcol, Lidx;
+        for (int64_t g = 0; g < n; ++g) {
+            const int64_t k = g / T;
+            for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
+                const int64_t j = ci[e];
+                if (k > 0 && j < k * T && j >= (k - 1) * T) {
+                    Lcol.push_back((int32_t)(j - (k - 1) * T));
+                    Lidx.push_back((int32_t)e);
+                }
+            }
+            Lptr[g + 1] = (int32_t)Lcol.size();
+        }
         auto up = [&](const char* name, const void* src, size_t bytes) -> void* {
             void* d = h->arena.get<unsigned char>(name, (int64_t)bytes);
             if (bytes) SIM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, h->st));
@@ -421,9 +436,13 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
         P.up_ptr = (const int32_t*)up("P_upp", up_ptr.data(), sizeof(int32_t) * up_ptr.size());
         P.up_row = (const int32_t*)up("P_upr", up_row.data(), sizeof(int32_t) * up_row.size());
         P.up_idx = (const int32_t*)up("P_upi", up_idx.data(), sizeof(int32_t) * up_idx.size());
+        P.Lptr = (const int32_t*)up("P_Lptr", Lptr.data(), sizeof(int32_t) * Lptr.size());
+        P.Lcol = (const int32_t*)up("P_Lcol", Lcol.data(), sizeof(int32_t) * Lcol.size());
+        P.Lidx = (const int32_t*)up("P_Lidx", Lidx.data(), sizeof(int32_t) * Lidx.size());
+        P.nnzL = (int64_t)Lcol.size();
         SIM_CUDA(cudaStreamSynchronize(h->st));
         const size_t cs = o.precision == SIM_FP64 ? sizeof(double2) : sizeof(float2);
-        h->factor_bytes = (size_t)2 * nb * (size_t)T * T * cs;
+        h->factor_bytes = ((size_t)2 * nb * (size_t)T * T + (size_t)P.nnzL + 16) * cs;
         ensure_shift_capacity(h.get());
         h->d_f = h->arena.get<double2>("f", n);
         h->stats.n = n;
@@ -819,7 +838,8 @@ sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const d
         factor_storage(h, sc);
         int* d_list = h->arena.get<int>("cmp_list", 1);
         SIM_CUDA(cudaMemcpyAsync(d_list, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
-        factor_shifts(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st);
+        if (!factor_shifts_cluster(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st))
+            factor_shifts(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st);
         JobSpace js = make_jobspace(h, 1, "cmp_");
         js.h_jobshift = &sc;
         SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));

@@ -34,7 +34,17 @@ struct Pencil {
     const int32_t* up_ptr = nullptr;
     const int32_t* up_row = nullptr;
     const int32_t* up_idx = nullptr;
+    // couplings to block row k-1, per row g: entries [Lptr[g], Lptr[g+1]) with
+    // column Lcol (relative to the start of block k-1) and value index Lidx.
+    // Each shift's factor stores the shifted values Lval (after E).
+    const int32_t* Lptr = nullptr;
+    const int32_t* Lcol = nullptr;
+    const int32_t* Lidx = nullptr;
+    int64_t nnzL = 0;
 };
+
+// Offset (in elements of the factor type) of Lval inside a shift's factor.
+__host__ __device__ inline size_t factor_lval_offset(const Pencil& P) { return (size_t)2 * P.nb * P.T * P.T; }
 
 // Workspace of a batch of Krylov jobs (one job = one Arnoldi process for
 // one shift and one starting vector).  All vectors are complex128 of length n,

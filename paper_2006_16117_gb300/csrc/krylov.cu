@@ -62,10 +62,15 @@ __global__ void __launch_bounds__(FACTOR_THREADS) k_factor(Pencil P, const int* 
     const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
     const size_t TT = (size_t)T * T;
 
+    {
+        C* Lval = Dinv + factor_lval_offset(P);
+        for (int64_t e = tid; e < P.nnzL; e += bd) Lval[e] = from_c128<C>(shifted_val(P, P.Lidx[e], sg));
+    }
     for (int k = 0; k < nb; ++k) {
         C* D = Dinv + (size_t)k * TT;
         const int64_t g0 = (int64_t)k * T;
-        for (size_t e = tid; e < TT; e += bd) D[e] = czero<C>();
+        for (int i = warp; i < T; i += nw)
+            for (int c = lane; c < T; c += 32) D[(size_t)i * T + c] = czero<C>();
         __syncthreads();
         for (int i = tid; i < T; i += bd) {
             int64_t g = g0 + i;
@@ -81,18 +86,16 @@ __global__ void __launch_bounds__(FACTOR_THREADS) k_factor(Pencil P, const int* 
         __syncthreads();
         if (k > 0) {
             const C* Ep = E + (size_t)(k - 1) * TT;
-            const int64_t gp = g0 - T;
-            for (size_t el = tid; el < TT; el += bd) {
-                int i = (int)(el / T), c = (int)(el % T);
-                int64_t g = g0 + i;
+            const C* Lval = Dinv + factor_lval_offset(P);
+            for (int i = warp; i < T; i += nw) {
+                const int64_t g = g0 + i;
                 if (g >= P.n) continue;
-                C acc = czero<C>();
-                for (int64_t e = P.rp[g]; e < P.rp[g + 1]; ++e) {
-                    int64_t j = P.ci[e];
-                    if (j >= g0) break;
-                    if (j >= gp) acc = cfma(from_c128<C>(shifted_val(P, e, sg)), Ep[(size_t)(j - gp) * T + c], acc);
+                const int e0 = P.Lptr[g], e1 = P.Lptr[g + 1];
+                for (int c = lane; c < T; c += 32) {
+                    C acc = czero<C>();
+                    for (int e = e0; e < e1; ++e) acc = cfma(Lval[e], Ep[(size_t)P.Lcol[e] * T + c], acc);
+                    D[(size_t)i * T + c] = csub(D[(size_t)i * T + c], acc);
                 }
-                D[el] = csub(D[el], acc);
             }
             __syncthreads();
         }
@@ -137,17 +140,19 @@ __global__ void __launch_bounds__(FACTOR_THREADS) k_factor(Pencil P, const int* 
                 colp[c] = D[(size_t)c * T + p];
             }
             __syncthreads();
-            for (size_t el = tid; el < TT; el += bd) {
-                int i = (int)(el / T), c = (int)(el % T);
+            for (int i = warp; i < T; i += nw) {
+                C* Di = D + (size_t)i * T;
                 if (i == p) {
-                    D[el] = rowp[c];
+                    for (int c = lane; c < T; c += 32) Di[c] = rowp[c];
                 } else {
-                    C base = (c == p) ? czero<C>() : D[el];
-                    C f = colp[i];
-                    C rp = rowp[c];
-                    base.x -= f.x * rp.x - f.y * rp.y;
-                    base.y -= f.x * rp.y + f.y * rp.x;
-                    D[el] = base;
+                    const C f = colp[i];
+                    for (int c = lane; c < T; c += 32) {
+                        C base = (c == p) ? czero<C>() : Di[c];
+                        const C rp = rowp[c];
+                        base.x -= f.x * rp.x - f.y * rp.y;
+                        base.y -= f.x * rp.y + f.y * rp.x;
+                        Di[c] = base;
+                    }
                 }
             }
             __syncthreads();
@@ -167,13 +172,13 @@ __global__ void __launch_bounds__(FACTOR_THREADS) k_factor(Pencil P, const int* 
         if (k < nb - 1) {
             C* Ek = E + (size_t)k * TT;
             const int32_t* cp = P.up_ptr + (size_t)k * (T + 1);
-            for (size_t el = tid; el < TT; el += bd) {
-                int rr = (int)(el / T), c = (int)(el % T);
-                C acc = czero<C>();
-                for (int q = cp[c]; q < cp[c + 1]; ++q)
-                    acc = cfma(D[(size_t)rr * T + P.up_row[q]], from_c128<C>(shifted_val(P, P.up_idx[q], sg)), acc);
-                Ek[el] = acc;
-            }
+            for (int rr = warp; rr < T; rr += nw)
+                for (int c = lane; c < T; c += 32) {
+                    C acc = czero<C>();
+                    for (int q = cp[c]; q < cp[c + 1]; ++q)
+                        acc = cfma(D[(size_t)rr * T + P.up_row[q]], from_c128<C>(shifted_val(P, P.up_idx[q], sg)), acc);
+                    Ek[(size_t)rr * T + c] = acc;
+                }
         }
         __syncthreads();
     }
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_block_solve(Pencil P, JobSpac
     const C* E = Dinv + (size_t)nb * T * T;
     const double2* in = js.vec + (size_t)job * js.vstride + (size_t)in_slot * js.n;
     double2* out = js.vec + (size_t)job * js.vstride + (size_t)out_slot * js.n;
-    const double2 sg = sigma[s];
+    
     extern __shared__ unsigned char smem_raw[];
     C* sb = reinterpret_cast<C*>(smem_raw);  // right-hand side block
     C* tp = sb + T;                          // previous t (forward) / next x (backward)
@@ -250,17 +255,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_block_solve(Pencil P, JobSpac
             C v = czero<C>();
             if (g < P.n) {
                 v = from_c128<C>(in[g]);
-                if (k > 0) {
-                    for (int64_t e = P.rp[g]; e < P.rp[g + 1]; ++e) {
-                        int64_t j = P.ci[e];
-                        if (j >= g0) break;
-                        if (j >= g0 - T) {
-                            C a = from_c128<C>(shifted_val(P, e, sg));
-                            C t = tp[j - (g0 - T)];
-                            v.x -= a.x * t.x - a.y * t.y;
-                            v.y -= a.x * t.y + a.y * t.x;
-                        }
-                    }
+                const C* Lval = Dinv + factor_lval_offset(P);
+                for (int e = P.Lptr[g]; e < P.Lptr[g + 1]; ++e) {
+                    const C a = Lval[e];
+                    const C t = tp[P.Lcol[e]];
+                    v.x -= a.x * t.x - a.y * t.y;
+                    v.y -= a.x * t.y + a.y * t.x;
                 }
             }
             sb[i] = v;

@@ -71,15 +71,11 @@ template <class C> __device__ __forceinline__ C zero_c();
 template <> __device__ __forceinline__ double2 zero_c<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 zero_c<float2>() { return make_float2(0.f, 0.f); }
 
-__device__ __forceinline__ double2 kval(const Pencil& P, int64_t e, double2 sg) {
-    const double2 a = P.Ka[e], b = P.Kb[e];
-    return make_double2(a.x - (sg.x * b.x - sg.y * b.y), a.y - (sg.x * b.y + sg.y * b.x));
-}
 
 }  // namespace
 
 template <class C, int R>
-__global__ void __launch_bounds__(256) k_block_solve_cl(Pencil P, JobSpace js, int in_slot, int out_slot,
+__global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js, int in_slot, int out_slot,
                                                         const double2* sigma, void* const* fptrs,
                                                         const int* grp_jobs, int SR, int NS, int* err) {
     cg::cluster_group cl = cg::this_cluster();
@@ -97,9 +93,9 @@ __global__ void __launch_bounds__(256) k_block_solve_cl(Pencil P, JobSpace js, i
         if (jb[j] >= 0) nr = j + 1;
     }
     const int s = js.d_jobshift[jb[0]];
-    const double2 sg = sigma[s];
     const C* Dinv = reinterpret_cast<const C*>(fptrs[s]);
     const C* E = Dinv + (size_t)nb * T * T;
+    const C* Lval = Dinv + factor_lval_offset(P);
 
     const int Tc = (T + Ccl - 1) / Ccl;
     const int r0 = min(T, q * Tc), r1 = min(T, r0 + Tc);
@@ -111,7 +107,8 @@ __global__ void __launch_bounds__(256) k_block_solve_cl(Pencil P, JobSpace js, i
     C* stage = reinterpret_cast<C*>(raw);                       // [NS][SR*T]
     C* vbuf = stage + (size_t)NS * SR * T;                      // [2][R][T]
     C* sbuf = vbuf + (size_t)2 * R * T;                         // [R][T]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sbuf + (size_t)R * T);
+    C* tbuf = sbuf + (size_t)R * T;                              // [R][T]: t_k rows of this CTA (backward)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tbuf + (size_t)R * T);
     __shared__ int s_fail;
 
     auto chunk_src = [&](int c, uint32_t& bytes) -> const C* {
@@ -149,6 +146,52 @@ __global__ void __launch_bounds__(256) k_block_solve_cl(Pencil P, JobSpace js, i
         out[j] = js.vec + (size_t)jj * js.vstride + (size_t)out_slot * js.n;
     }
 
+    // Register prefetch of the next step's chain-independent inputs: r_k and
+    // the first coupling of each row (forward), t_k of this CTA's rows (backward).
+    constexpr int PFN = 8;
+    const bool pf_ok = T * nr <= PFN * (int)blockDim.x;
+    C pf_v[PFN], pf_a[PFN];
+    int pf_c[PFN], pf_n[PFN];
+    auto prefetch_fwd = [&](int kk) {
+        const int64_t gg0 = (int64_t)kk * T;
+#pragma unroll
+        for (int t = 0; t < PFN; ++t) {
+            const int idx = tid + t * (int)blockDim.x;
+            pf_n[t] = -1;
+            if (idx < T * nr) {
+                const int i = idx % T, j = idx / T;
+                const int64_t g = gg0 + i;
+                if (g < P.n) {
+                    pf_v[t] = from_c128<C>(in[j][g]);
+                    const int e0 = P.Lptr[g], e1 = P.Lptr[g + 1];
+                    pf_n[t] = e1 - e0;
+                    if (e1 > e0) {
+                        pf_c[t] = P.Lcol[e0];
+                        pf_a[t] = Lval[e0];
+                    }
+                } else {
+                    pf_n[t] = -2;
+                }
+            }
+        }
+    };
+    auto prefetch_bwd = [&](int kk) {
+        const int64_t gg0 = (int64_t)kk * T + r0;
+#pragma unroll
+        for (int t = 0; t < PFN; ++t) {
+            const int idx = tid + t * (int)blockDim.x;
+            pf_n[t] = -1;
+            if (idx < myrows * nr) {
+                const int i = idx % myrows, j = idx / myrows;
+                const int64_t g = gg0 + i;
+                pf_v[t] = g < P.n ? from_c128<C>(out[j][g]) : zero_c<C>();
+                pf_n[t] = 0;
+            }
+        }
+    };
+    const bool pfb_ok = myrows * nr <= PFN * (int)blockDim.x;
+    if (pf_ok) prefetch_fwd(0);
+
     int chunk = 0;
     for (int b = 0; b < 2 * nb - 1; ++b) {
         const bool fwd = b < nb;
@@ -157,25 +200,50 @@ __global__ void __launch_bounds__(256) k_block_solve_cl(Pencil P, JobSpace js, i
         const C* vprev = vbuf + (size_t)((b + 1) & 1) * R * T;  // t_{k-1} (fwd) or x_{k+1} (bwd)
         const int cur = b & 1;
         const bool failed = s_fail != 0;
-        if (fwd && !failed) {
+        if (fwd && !failed && pf_ok) {
             // s_k = r_k - L_k t_{k-1}: every CTA forms the whole block
+#pragma unroll
+            for (int t = 0; t < PFN; ++t) {
+                const int idx = tid + t * (int)blockDim.x;
+                if (idx >= T * nr) break;
+                const int i = idx % T, j = idx / T;
+                C v = zero_c<C>();
+                if (pf_n[t] >= 0) {
+                    v = pf_v[t];
+                    if (pf_n[t] >= 1) {
+                        const C a = pf_a[t];
+                        const C tt = vprev[(size_t)j * T + pf_c[t]];
+                        v.x -= a.x * tt.x - a.y * tt.y;
+                        v.y -= a.x * tt.y + a.y * tt.x;
+                    }
+                    if (pf_n[t] > 1) {
+                        const int64_t g = g0 + i;
+                        for (int e = P.Lptr[g] + 1; e < P.Lptr[g + 1]; ++e) {
+                            const C a = Lval[e];
+                            const C tt = vprev[(size_t)j * T + P.Lcol[e]];
+                            v.x -= a.x * tt.x - a.y * tt.y;
+                            v.y -= a.x * tt.y + a.y * tt.x;
+                        }
+                    }
+                }
+                sbuf[(size_t)j * T + i] = v;
+            }
+            __syncthreads();
+            if (k + 1 < nb) prefetch_fwd(k + 1);
+            else if (pfb_ok) prefetch_bwd(nb - 2 >= 0 ? nb - 2 : 0);
+        } else if (fwd && !failed) {
             for (int idx = tid; idx < T * nr; idx += blockDim.x) {
                 const int i = idx % T, j = idx / T;
                 const int64_t g = g0 + i;
                 C v = zero_c<C>();
                 if (g < P.n) {
                     v = from_c128<C>(in[j][g]);
-                    if (k > 0) {
-                        for (int64_t e = P.rp[g]; e < P.rp[g + 1]; ++e) {
-                            const int64_t c = P.ci[e];
-                            if (c >= g0) break;
-                            if (c >= g0 - T) {
-                                const C a = from_c128<C>(kval(P, e, sg));
-                                const C t = vprev[(size_t)j * T + (c - (g0 - T))];
-                                v.x -= a.x * t.x - a.y * t.y;
-                                v.y -= a.x * t.y + a.y * t.x;
-                            }
-                        }
+                    const int e0 = P.Lptr[g], e1 = P.Lptr[g + 1];
+                    for (int e = e0; e < e1; ++e) {
+                        const C a = Lval[e];
+                        const C t = vprev[(size_t)j * T + P.Lcol[e]];
+                        v.x -= a.x * t.x - a.y * t.y;
+                        v.y -= a.x * t.y + a.y * t.x;
                     }
                 }
                 sbuf[(size_t)j * T + i] = v;
@@ -183,6 +251,23 @@ __global__ void __launch_bounds__(256) k_block_solve_cl(Pencil P, JobSpace js, i
             __syncthreads();
         }
         const C* rhs = fwd ? sbuf : vprev;
+        if (!fwd && !failed) {
+            // t_k of this CTA's rows, for x_k = t_k - E_k x_{k+1}
+            if (pfb_ok) {
+#pragma unroll
+                for (int t = 0; t < PFN; ++t) {
+                    const int idx = tid + t * (int)blockDim.x;
+                    if (idx < myrows * nr) tbuf[(size_t)(idx / myrows) * T + idx % myrows] = pf_v[t];
+                }
+                if (k > 0) prefetch_bwd(k - 1);
+            } else {
+                for (int idx = tid; idx < myrows * nr; idx += blockDim.x) {
+                    const int i = idx % myrows, j = idx / myrows;
+                    const int64_t g = g0 + r0 + i;
+                    tbuf[(size_t)j * T + i] = g < P.n ? from_c128<C>(out[j][g]) : zero_c<C>();
+                }
+            }
+        }
         for (int sub = 0; sub < nsub; ++sub, ++chunk) {
             const int slot = chunk % NS;
             if (!s_fail) {
@@ -201,36 +286,47 @@ __global__ void __launch_bounds__(256) k_block_solve_cl(Pencil P, JobSpace js, i
                 const C* M = stage + (size_t)slot * SR * T;
                 const int rs = r0 + sub * SR;
                 const int rows = min(SR, r1 - rs);
-                for (int rr = warp; rr < rows; rr += nw) {
-                    C acc[R];
+                constexpr int RP = R == 1 ? 4 : (R == 2 ? 2 : 1);  // rows per warp pass
+                for (int rb = warp * RP; rb < rows; rb += nw * RP) {
+                    C acc[RP][R];
 #pragma unroll
-                    for (int j = 0; j < R; ++j) acc[j] = zero_c<C>();
-                    const C* row = M + (size_t)rr * T;
+                    for (int p = 0; p < RP; ++p)
+#pragma unroll
+                        for (int j = 0; j < R; ++j) acc[p][j] = zero_c<C>();
                     for (int c = lane; c < T; c += 32) {
-                        const C m = row[c];
+                        C xv[R];
 #pragma unroll
-                        for (int j = 0; j < R; ++j)
-                            if (j < nr) acc[j] = cfma(m, rhs[(size_t)j * T + c], acc[j]);
+                        for (int j = 0; j < R; ++j) xv[j] = (j < nr) ? rhs[(size_t)j * T + c] : zero_c<C>();
+#pragma unroll
+                        for (int p = 0; p < RP; ++p) {
+                            if (rb + p < rows) {
+                                const C m = M[(size_t)(rb + p) * T + c];
+#pragma unroll
+                                for (int j = 0; j < R; ++j) acc[p][j] = cfma(m, xv[j], acc[p][j]);
+                            }
+                        }
                     }
 #pragma unroll
-                    for (int j = 0; j < R; ++j)
-                        if (j < nr) acc[j] = warp_sum(acc[j]);
-                    const int r = rs + rr;
-                    const int64_t g = g0 + r;
-                    if (lane < nr) {
-                        C val = acc[0];
+                    for (int p = 0; p < RP; ++p)
 #pragma unroll
-                        for (int j = 1; j < R; ++j)
-                            if (lane == j) val = acc[j];
-                        const int j = lane;
-                        if (!fwd) {
-                            const C t = g < P.n ? from_c128<C>(out[j][g]) : zero_c<C>();
-                            val = csub(t, val);
-                        }
-                        if (g < P.n) out[j][g] = to_c128(val);
-                        for (int qq = 0; qq < Ccl; ++qq) {
-                            C* dst = cl.map_shared_rank(vbuf + (size_t)cur * R * T + (size_t)j * T + r, qq);
-                            *dst = val;
+                        for (int j = 0; j < R; ++j) acc[p][j] = warp_sum(acc[p][j]);
+#pragma unroll
+                    for (int p = 0; p < RP; ++p) {
+                        if (rb + p >= rows) break;
+                        const int r = rs + rb + p;
+                        const int64_t g = g0 + r;
+                        if (lane < nr) {
+                            C val = acc[p][0];
+#pragma unroll
+                            for (int j = 1; j < R; ++j)
+                                if (lane == j) val = acc[p][j];
+                            const int j = lane;
+                            if (!fwd) val = csub(tbuf[(size_t)j * T + (r - r0)], val);
+                            if (g < P.n) out[j][g] = to_c128(val);
+                            for (int qq = 0; qq < Ccl; ++qq) {
+                                C* dst = cl.map_shared_rank(vbuf + (size_t)cur * R * T + (size_t)j * T + r, qq);
+                                *dst = val;
+                            }
                         }
                     }
                 }
@@ -270,7 +366,7 @@ bool make_plan(int T, size_t cs, int want_R, Plan& p) {
     const size_t budget = 220 * 1024;
     for (int R : {8, 4, 2, 1}) {
         if (R > want_R && R != 1) continue;
-        const size_t vec = (size_t)3 * R * T * cs;
+        const size_t vec = (size_t)4 * R * T * cs;
         if (vec + 64 >= budget) continue;
         const int NS = 3;
         const size_t per_row = (size_t)NS * T * cs;
@@ -354,6 +450,12 @@ bool block_solve_cluster(const Pencil& P, int precision, const JobSpace& js, con
     int Ccl = 8;
     while (Ccl > 1 && (int64_t)Ccl * ng > 152) Ccl >>= 1;
     Ccl = std::min(Ccl, P.T);
+    {
+        // equal chunks: a CTA's rows in as few stages-worth pieces as the ring allows
+        const int Tc = (P.T + Ccl - 1) / Ccl;
+        const int nsub = (Tc + pl.SR - 1) / pl.SR;
+        pl.SR = (Tc + nsub - 1) / nsub;
+    }
     const double TT = (double)P.T * P.T, blocks = 2.0 * P.nb - 1.0;
     kprof_begin("block_solve", st);
 #define SIM_LAUNCH_R(CT, RR) \
