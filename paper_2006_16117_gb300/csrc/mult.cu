@@ -217,7 +217,7 @@ std::vector<int> multiplicities(const MultInput& in, bool& ok) {
     for (int c = 0; c < C; ++c) pending[c] = c;
     int k = o.mult_k;
     const int kin = std::max(1, std::min(o.inner_restart, 32));
-    constexpr int JMAX = 256;
+    constexpr int JMAX = 512;  // jobs per batch: all shifts of a 64-vector pass at once up to 64 shifts
     while (!pending.empty()) {
         double2* F = ar.get<double2>("mu_F", (int64_t)k * n);
         random_vectors(o.mult_seed, n, k, 0, F, n, st);

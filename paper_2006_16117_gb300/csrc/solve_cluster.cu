@@ -67,6 +67,29 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 
 constexpr long long WAIT_LIMIT = 1ll << 26;  // try_wait polls before a wait is declared failed
 
+// Sum S values across the warp (S = 8 or 16): at each stage a lane keeps half
+// of its values and trades the other half with its partner, so S-1 shuffles
+// leave one partial per lane; the lanes below the value bits then finish with
+// plain xor shuffles.  Afterwards lane L holds, in v[0], the warp sum of value
+// (L >> (5 - log2 S)) & (S - 1).
+template <class Rt, int S> __device__ __forceinline__ void butterfly(Rt (&v)[S], int lane) {
+#pragma unroll
+    for (int st = 0, width = S; width > 1; ++st, width >>= 1) {
+        const int mask = 16 >> st;
+        const bool upper = (lane & mask) != 0;
+        const int half = width >> 1;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const Rt send = upper ? v[i] : v[i + half];
+            const Rt keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+        }
+    }
+    constexpr int LOGS = S == 16 ? 4 : 3;
+#pragma unroll
+    for (int mask = (1 << (5 - LOGS)) >> 1; mask > 0; mask >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], mask);
+}
+
 template <class C> __device__ __forceinline__ C zero_c();
 template <> __device__ __forceinline__ double2 zero_c<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 zero_c<float2>() { return make_float2(0.f, 0.f); }
@@ -287,40 +310,49 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
                 const int rs = r0 + sub * SR;
                 const int rows = min(SR, r1 - rs);
                 constexpr int RP = R == 1 ? 4 : (R == 2 ? 2 : 1);  // rows per warp pass
+                constexpr int NSC = 2 * RP * R;                      // real accumulators per lane
+                constexpr int LOGS = NSC == 16 ? 4 : 3;
+                constexpr int SH = 5 - LOGS;                         // lane bits below the value index
+                using Rt = decltype(zero_c<C>().x);
                 for (int rb = warp * RP; rb < rows; rb += nw * RP) {
-                    C acc[RP][R];
+                    Rt acc[NSC];
 #pragma unroll
-                    for (int p = 0; p < RP; ++p)
-#pragma unroll
-                        for (int j = 0; j < R; ++j) acc[p][j] = zero_c<C>();
+                    for (int u = 0; u < NSC; ++u) acc[u] = Rt(0);
                     for (int c = lane; c < T; c += 32) {
                         C xv[R];
 #pragma unroll
-                        for (int j = 0; j < R; ++j) xv[j] = (j < nr) ? rhs[(size_t)j * T + c] : zero_c<C>();
+                        for (int j = 0; j < R; ++j) xv[j] = rhs[(size_t)j * T + c];  // consecutive across lanes
 #pragma unroll
                         for (int p = 0; p < RP; ++p) {
                             if (rb + p < rows) {
                                 const C m = M[(size_t)(rb + p) * T + c];
 #pragma unroll
-                                for (int j = 0; j < R; ++j) acc[p][j] = cfma(m, xv[j], acc[p][j]);
+                                for (int j = 0; j < R; ++j) {
+                                    Rt& re = acc[(p * R + j) * 2];
+                                    Rt& im = acc[(p * R + j) * 2 + 1];
+                                    re = fma(m.x, xv[j].x, re);
+                                    re = fma(-m.y, xv[j].y, re);
+                                    im = fma(m.x, xv[j].y, im);
+                                    im = fma(m.y, xv[j].x, im);
+                                }
                             }
                         }
                     }
-#pragma unroll
-                    for (int p = 0; p < RP; ++p)
-#pragma unroll
-                        for (int j = 0; j < R; ++j) acc[p][j] = warp_sum(acc[p][j]);
-#pragma unroll
-                    for (int p = 0; p < RP; ++p) {
-                        if (rb + p >= rows) break;
-                        const int r = rs + rb + p;
-                        const int64_t g = g0 + r;
-                        if (lane < nr) {
-                            C val = acc[p][0];
-#pragma unroll
-                            for (int j = 1; j < R; ++j)
-                                if (lane == j) val = acc[p][j];
-                            const int j = lane;
+                    // butterfly: NSC sums over the warp with NSC shuffles in all;
+                    // lane L ends with the sum of value (L >> SH) & (NSC - 1)
+                    butterfly<Rt, NSC>(acc, lane);
+                    const Rt mine = acc[0];
+                    const Rt other = __shfl_xor_sync(0xffffffffu, mine, 1 << SH);
+                    const int kv = (lane >> SH) & (NSC - 1);
+                    if ((lane & ((1 << SH) - 1)) == 0 && (kv & 1) == 0) {
+                        const int pair = kv >> 1;
+                        const int p = pair / R, j = pair % R;
+                        if (rb + p < rows && j < nr) {
+                            const int r = rs + rb + p;
+                            const int64_t g = g0 + r;
+                            C val;
+                            val.x = mine;
+                            val.y = other;
                             if (!fwd) val = csub(tbuf[(size_t)j * T + (r - r0)], val);
                             if (g < P.n) out[j][g] = to_c128(val);
                             for (int qq = 0; qq < Ccl; ++qq) {
@@ -386,7 +418,11 @@ void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, c
                void* const* fptrs, const int* d_grp, int ngroups, int Ccl, const Plan& pl, int* d_err,
                cudaStream_t st) {
     auto kern = k_block_solve_cl<C, R>;
-    SIM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    static size_t attr_set = 0;  // per instantiation
+    if (pl.smem > attr_set) {
+        SIM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+        attr_set = pl.smem;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ngroups * Ccl);
     cfg.blockDim = dim3(256);
@@ -406,6 +442,11 @@ void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, c
 int* g_err = nullptr;
 int* g_grp = nullptr;
 int g_grp_cap = 0;
+// pinned staging for the group table: a pageable upload would synchronise the stream
+int* g_grp_h[2] = {nullptr, nullptr};
+cudaEvent_t g_grp_ev[2] = {nullptr, nullptr};
+int g_grp_h_cap = 0;
+int g_grp_flip = 0;
 
 }  // namespace
 
@@ -441,11 +482,29 @@ bool block_solve_cluster(const Pencil& P, int precision, const JobSpace& js, con
         SIM_CUDA(cudaMemset(g_err, 0, sizeof(int)));
     }
     if ((int)flat.size() > g_grp_cap) {
-        if (g_grp) cudaFree(g_grp);
+        if (g_grp) {
+            SIM_CUDA(cudaStreamSynchronize(st));
+            cudaFree(g_grp);
+        }
         g_grp_cap = (int)flat.size() * 2;
-        SIM_CUDA(cudaMalloc(&g_grp, sizeof(int) * g_grp_cap));
+        SIM_CUDA(cudaMalloc(&g_grp, sizeof(int) * g_grp_cap * 2));
     }
-    SIM_CUDA(cudaMemcpyAsync(g_grp, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, st));
+    if ((int)flat.size() > g_grp_h_cap) {
+        for (int b = 0; b < 2; ++b) {
+            if (g_grp_ev[b]) SIM_CUDA(cudaEventSynchronize(g_grp_ev[b]));
+            if (g_grp_h[b]) cudaFreeHost(g_grp_h[b]);
+            SIM_CUDA(cudaMallocHost(&g_grp_h[b], sizeof(int) * flat.size() * 2));
+            if (!g_grp_ev[b]) SIM_CUDA(cudaEventCreateWithFlags(&g_grp_ev[b], cudaEventDisableTiming));
+        }
+        g_grp_h_cap = (int)flat.size() * 2;
+    }
+    const int fb = g_grp_flip;
+    g_grp_flip ^= 1;
+    SIM_CUDA(cudaEventSynchronize(g_grp_ev[fb]));  // the copy that last used this buffer is done
+    std::copy(flat.begin(), flat.end(), g_grp_h[fb]);
+    int* d_grp = g_grp + (size_t)fb * g_grp_cap;
+    SIM_CUDA(cudaMemcpyAsync(d_grp, g_grp_h[fb], sizeof(int) * flat.size(), cudaMemcpyHostToDevice, st));
+    SIM_CUDA(cudaEventRecord(g_grp_ev[fb], st));
     // cluster size: as many CTAs per group as the 152 SMs allow, up to 8
     int Ccl = 8;
     while (Ccl > 1 && (int64_t)Ccl * ng > 152) Ccl >>= 1;
@@ -459,7 +518,7 @@ bool block_solve_cluster(const Pencil& P, int precision, const JobSpace& js, con
     const double TT = (double)P.T * P.T, blocks = 2.0 * P.nb - 1.0;
     kprof_begin("block_solve", st);
 #define SIM_LAUNCH_R(CT, RR) \
-    launch_cl<CT, RR>(P, js, in_slot, out_slot, d_sigma, d_factor_ptrs, g_grp, ng, Ccl, pl, g_err, st)
+    launch_cl<CT, RR>(P, js, in_slot, out_slot, d_sigma, d_factor_ptrs, d_grp, ng, Ccl, pl, g_err, st)
     if (precision == SIM_FP64) {
         if (pl.R == 8) SIM_LAUNCH_R(double2, 8);
         else if (pl.R == 4) SIM_LAUNCH_R(double2, 4);
