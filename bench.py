@@ -152,14 +152,16 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def traffic_record(kernel: str, precision: str):
-    """DRAM bytes per launch of the kernel from the committed ncu summary (or None)."""
+def traffic_record(kernel: str, precision: str, algorithmic_bytes_per_launch: float):
+    """DRAM bytes per launch: the committed ncu captures give DRAM bytes over
+    algorithmic bytes for this kernel (traffic grows with the groups a launch
+    processes), scaled here to the average launch of the timed steps."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
-            rec = json.load(fh)
-        return rec.get("%s:%s" % (kernel, precision))
-    except (OSError, ValueError):
+            rec = json.load(fh).get("%s:%s" % (kernel, precision))
+        return rec["dram_over_algorithmic"] * algorithmic_bytes_per_launch if rec else None
+    except (OSError, ValueError, KeyError):
         return None
 
 
@@ -351,7 +353,8 @@ def run_ours(args, world, rank, local):
         achieved = k["bytes"] / (k["ms"] / 1000.0) / 1e9
         line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                            "traffic": traffic_record(top, "mixed"), "peak_source": src,
+                            "traffic": traffic_record(top, "mixed", k["bytes"] / max(1, k["launches"])),
+                            "peak_source": src,
                             "avg_launch_ms": k["ms"] / max(1, k["launches"]),
                             "bytes_per_launch": k["bytes"] / max(1, k["launches"])}
     else:
