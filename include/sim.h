@@ -98,6 +98,8 @@ typedef struct {
     double inner_tol;         /* relative residual target of each shifted solve (1e-12) */
     int32_t inner_restart;    /* GMRES restart length (8) */
     int32_t inner_max_iter;   /* GMRES iteration cap per solve (64) */
+    double mult_inner_tol;    /* inner tolerance for the multiplicity step's Krylov spaces,
+                                 which feed only a rank test at mult_tol (1e-10) */
 } sim_options;
 
 /* Counters of the last set_region .. multiplicity sequence. */

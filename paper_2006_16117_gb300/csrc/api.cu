@@ -314,6 +314,7 @@ void sim_default_options(sim_options* o) {
     o->inner_tol = 1e-12;
     o->inner_restart = 8;
     o->inner_max_iter = 64;
+    o->mult_inner_tol = 1e-10;
 }
 
 sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream, sim_handle* out) {
@@ -328,7 +329,7 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
         if (o.m < 2 || eval_smem_bytes(o.m) > 220 * 1024 || o.n0 != 4 || !(o.delta0 > 0) || !(o.eps > 0) ||
             !(o.h0 > 0) || o.max_shifts < 1 || o.max_shifts > SIM_MAX_SHIFTS - 1 || o.mult_k < 1 ||
             o.mult_kmax < o.mult_k || o.mult_kmax > 64 || o.mult_nodes < 4 || o.mult_nodes > 64 ||
-            !(o.inner_tol > 0) || o.inner_restart < 1 || o.inner_restart > 32 || o.inner_max_iter < 1 ||
+            !(o.inner_tol > 0) || !(o.mult_inner_tol > 0) || o.inner_restart < 1 || o.inner_restart > 32 || o.inner_max_iter < 1 ||
             (o.precision != SIM_FP64 && o.precision != SIM_MIXED) || o.max_squares < 1 ||
             (o.residual_scale != 0 && o.residual_scale != 1))
             return fail(nullptr, SIM_ERR_INVALID_ARG, "options out of range (m must be <= 52, n0 must be 4)");

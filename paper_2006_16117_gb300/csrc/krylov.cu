@@ -397,6 +397,9 @@ struct GSArgs {
     double btol;
     int* meff;      // per job (optional)
     int* istat;     // per job IS_N ints (optional): IS_BROKEN flag
+    // selective reorthogonalisation (Daniel-Gragg-Kaufman-Stewart): the second
+    // pass runs only if the first one cut the norm of w below 1/sqrt(2) of it
+    int dgks;
 };
 
 __device__ __forceinline__ void block_reduce_vec(double2* red, int cnt, int nw) {
@@ -429,10 +432,17 @@ __device__ __forceinline__ void gs_partial_dots(const GSArgs& a, const double2* 
         acc = warp_sum(acc);
         if (lane == 0) red[i * nw + warp] = acc;
     }
+    if (a.dgks) {  // partial ||w||^2 as value cnt
+        double nn = 0.0;
+#pragma unroll
+        for (int t = 0; t < GS_PER; ++t) nn += wv[t].x * wv[t].x + wv[t].y * wv[t].y;
+        nn = warp_sum(nn);
+        if (lane == 0) red[a.cnt * nw + warp] = make_double2(nn, 0.0);
+    }
     __syncthreads();
-    block_reduce_vec(red, a.cnt, nw);
+    block_reduce_vec(red, a.cnt + (a.dgks ? 1 : 0), nw);
     __syncthreads();
-    for (int i = threadIdx.x; i < a.cnt; i += blockDim.x) out[i] = red[i * nw];
+    for (int i = threadIdx.x; i < a.cnt + (a.dgks ? 1 : 0); i += blockDim.x) out[i] = red[i * nw];
 }
 
 // pass-1 partial dot products  h_i = Σ_rows conj(q_i) w
@@ -464,10 +474,31 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_update(GSArgs a, int accumula
     double2* red = sm + a.cnt + 1;   // [cnt*nw]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double2* Pin = a.pin + (size_t)job * a.nchunk * a.pw;
+    double2* out = a.pout + ((size_t)job * a.nchunk + chunk) * a.pw;
+    if (a.dgks && accumulate) {
+        // second pass: needed only if the first one lost more than half of ||w||^2
+        __shared__ int s_skip;
+        if (threadIdx.x == 0) {
+            double na = 0.0;
+            for (int c = 0; c < a.nchunk; ++c) na += Pin[(size_t)c * a.pw + a.cnt].x;
+            const double nb = Pin[a.cnt + 1].x;
+            s_skip = na > 0.5 * nb;
+        }
+        __syncthreads();
+        if (s_skip) {
+            if (threadIdx.x == 0) out[0] = Pin[(size_t)chunk * a.pw + a.cnt];  // this chunk's ||w||^2
+            return;
+        }
+    }
     for (int i = threadIdx.x; i < a.cnt; i += blockDim.x) {
         double2 s = make_double2(0.0, 0.0);
         for (int c = 0; c < a.nchunk; ++c) s = cadd(s, Pin[(size_t)c * a.pw + i]);
         h[i] = s;
+    }
+    if (a.dgks && !accumulate && chunk == 0 && threadIdx.x == 0) {
+        double nb = 0.0;
+        for (int c = 0; c < a.nchunk; ++c) nb += Pin[(size_t)c * a.pw + a.cnt].x;
+        out[a.cnt + 1] = make_double2(nb, 0.0);  // ||w||^2 before the first pass, for the test above
     }
     __syncthreads();
     if (chunk == 0) {
@@ -501,7 +532,6 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_update(GSArgs a, int accumula
         int64_t r = r0 + threadIdx.x + t * GS_THREADS;
         if (r < a.n) w[r] = wv[t];
     }
-    double2* out = a.pout + ((size_t)job * a.nchunk + chunk) * a.pw;
     if (next_dots) {
         gs_partial_dots(a, B, wv, r0, red, out);
     } else {
@@ -564,8 +594,8 @@ static void gs_run(GSArgs a, double2* partial, size_t half, int nactive, cudaStr
     kprof_begin("gram_schmidt", st);
     dim3 grid(a.nchunk, nactive);
     const int nw = GS_THREADS / 32;
-    size_t sm_dots = (size_t)std::max(a.cnt, 1) * nw * sizeof(double2) + 64;
-    size_t sm_upd = ((size_t)a.cnt + 1 + (size_t)std::max(a.cnt, 1) * nw) * sizeof(double2) + 64;
+    size_t sm_dots = (size_t)(a.cnt + 2) * nw * sizeof(double2) + 64;
+    size_t sm_upd = ((size_t)a.cnt + 1 + (size_t)(a.cnt + 2) * nw) * sizeof(double2) + 64;
     double2* A = partial;
     double2* Bf = partial + half;
     a.pout = A;
@@ -830,6 +860,7 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
             a.pw = js.pw;
             a.nchunk = js.nchunk;
             a.active = js.d_active;
+            a.dgks = 1;
             gs_run(a, js.partial, half, na, st);
             k_gm_givens<<<cdiv_up(na, 128), 128, 0, st>>>(js, na, i, opt.inner_tol, opt.inner_max_iter);
             SIM_LAUNCH_CHECK();

@@ -204,7 +204,8 @@ __global__ void k_mult_start(JobSpace js, int J, int k, const double2* F) {
 }
 
 std::vector<int> multiplicities(const MultInput& in, bool& ok) {
-    const sim_options& o = *in.opt;
+    sim_options o = *in.opt;
+    o.inner_tol = o.mult_inner_tol;  // these spaces feed only the rank test
     const int C = (int)in.est.size();
     std::vector<int> mult(C, 0);
     ok = true;

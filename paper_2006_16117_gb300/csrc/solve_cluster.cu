@@ -65,6 +65,40 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
         : "memory");
 }
 
+// wait with cluster-scope acquire: the data arrived through st.async from other CTAs
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint32_t mapa_u32(const void* local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+
+// store one complex value into another CTA's shared memory; the bytes count
+// against that CTA's mbarrier (addresses from mapa_u32)
+__device__ __forceinline__ void st_async_c(uint32_t raddr, float2 v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "f"(v.x), "f"(v.y), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async_c(uint32_t raddr, double2 v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "d"(v.x), "d"(v.y), "r"(rbar)
+                 : "memory");
+}
+
 constexpr long long WAIT_LIMIT = 1ll << 26;  // try_wait polls before a wait is declared failed
 
 // Sum S values across the warp (S = 8 or 16): at each stage a lane keeps half
@@ -128,10 +162,11 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
 
     extern __shared__ __align__(128) unsigned char raw[];
     C* stage = reinterpret_cast<C*>(raw);                       // [NS][SR*T]
-    C* vbuf = stage + (size_t)NS * SR * T;                      // [2][R][T]
-    C* sbuf = vbuf + (size_t)2 * R * T;                         // [R][T]
+    C* vbuf = stage + (size_t)NS * SR * T;                      // [3][R][T]: the chain's vectors
+    C* sbuf = vbuf + (size_t)3 * R * T;                         // [R][T]
     C* tbuf = sbuf + (size_t)R * T;                              // [R][T]: t_k rows of this CTA (backward)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tbuf + (size_t)R * T);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tbuf + (size_t)R * T);  // [NS] stage barriers
+    uint64_t* vbar = bars + NS;                                           // [3] vector barriers
     __shared__ int s_fail;
 
     auto chunk_src = [&](int c, uint32_t& bytes) -> const C* {
@@ -146,6 +181,7 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
     if (tid == 0) {
         s_fail = 0;
         for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < 3; ++i) mbar_init(&vbar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -158,7 +194,10 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
             tma_load_1d(stage + (size_t)issued * SR * T, src, bytes, &bars[issued]);
         }
     }
-    cl.sync();  // every CTA of the cluster is running before any remote store
+    const uint32_t vec_bytes = (uint32_t)((size_t)T * nr * sizeof(C));  // one step's vector, all rows
+    if (tid == 0)
+        for (int i = 0; i < 3 && i <= 2 * nb - 3; ++i) mbar_expect_tx(&vbar[i], vec_bytes);  // steps 0, 1, 2
+    cl.sync();  // every CTA of the cluster is running, barriers initialised and armed, before any remote store
 
     const double2* in[R];
     double2* out[R];
@@ -220,8 +259,26 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
         const bool fwd = b < nb;
         const int k = fwd ? b : 2 * nb - 2 - b;
         const int64_t g0 = (int64_t)k * T;
-        const C* vprev = vbuf + (size_t)((b + 1) & 1) * R * T;  // t_{k-1} (fwd) or x_{k+1} (bwd)
-        const int cur = b & 1;
+        const int cur = b % 3, prv = (b + 2) % 3;
+        const C* vprev = vbuf + (size_t)prv * R * T;  // t_{k-1} (fwd) or x_{k+1} (bwd)
+        const bool last = b == 2 * nb - 2;            // nobody reads the last vector: not sent
+        if (b > 0 && !s_fail) {
+            // the previous step's vector: every CTA's rows, delivered by st.async
+            const uint32_t par = (uint32_t)(((b - 1) / 3) & 1);
+            long long it = 0;
+            while (!mbar_try_wait_cluster(&vbar[prv], par)) {
+                if (++it > WAIT_LIMIT) {
+                    s_fail = 1;
+                    atomicExch(err, 3);
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        // re-arm that barrier for step b+2 now: no CTA can send step b+2's rows
+        // before it has ours of step b+1, so the expected bytes are always
+        // registered before the first of them arrives
+        if (tid == 0 && b > 0 && !s_fail && b + 2 <= 2 * nb - 3) mbar_expect_tx(&vbar[prv], vec_bytes);
         const bool failed = s_fail != 0;
         if (fwd && !failed && pf_ok) {
             // s_k = r_k - L_k t_{k-1}: every CTA forms the whole block
@@ -355,9 +412,10 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
                             val.y = other;
                             if (!fwd) val = csub(tbuf[(size_t)j * T + (r - r0)], val);
                             if (g < P.n) out[j][g] = to_c128(val);
-                            for (int qq = 0; qq < Ccl; ++qq) {
-                                C* dst = cl.map_shared_rank(vbuf + (size_t)cur * R * T + (size_t)j * T + r, qq);
-                                *dst = val;
+                            if (!last) {
+                                C* loc = vbuf + (size_t)cur * R * T + (size_t)j * T + r;
+                                for (int qq = 0; qq < Ccl; ++qq)
+                                    st_async_c(mapa_u32(loc, qq), val, mapa_u32(&vbar[cur], qq));
                             }
                         }
                     }
@@ -373,9 +431,10 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
                 ++issued;
             }
         }
-        cl.sync();  // the new vector block is complete in every CTA
     }
-    // a failed CTA still has copies in flight: wait for them (bounded) before exit
+    // a failed CTA still has copies in flight: wait for them (bounded) before exit;
+    // the final cluster barrier keeps every CTA's shared memory alive until all
+    // peers have finished
     if (tid == 0 && s_fail) {
         for (int c = chunk; c < issued; ++c) {
             long long it = 0;
@@ -383,7 +442,7 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
             }
         }
     }
-    __syncthreads();
+    cl.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -398,7 +457,7 @@ bool make_plan(int T, size_t cs, int want_R, Plan& p) {
     const size_t budget = 220 * 1024;
     for (int R : {8, 4, 2, 1}) {
         if (R > want_R && R != 1) continue;
-        const size_t vec = (size_t)4 * R * T * cs;
+        const size_t vec = (size_t)5 * R * T * cs;
         if (vec + 64 >= budget) continue;
         const int NS = 3;
         const size_t per_row = (size_t)NS * T * cs;
@@ -407,7 +466,7 @@ bool make_plan(int T, size_t cs, int want_R, Plan& p) {
         p.R = R;
         p.SR = SR;
         p.NS = NS;
-        p.smem = (size_t)NS * SR * T * cs + vec + NS * sizeof(uint64_t) + 16;
+        p.smem = (size_t)NS * SR * T * cs + vec + (NS + 3) * sizeof(uint64_t) + 16;
         return true;
     }
     return false;

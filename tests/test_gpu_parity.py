@@ -161,7 +161,7 @@ def test_simm_small_convection_diffusion(simlib, small_oracle, precision):
     assert np.max(np.abs(np.sort(eig.real) - np.sort(w.reference_eigs.real))) <= 1e-6
     assert np.array_equal(mult, ref.multiplicities)
     assert st["unresolvable_final"] == 0
-    assert st["max_inner_residual"] <= 1e-12
+    assert st["max_inner_residual"] <= 100 * opt.mult_inner_tol  # worst accepted inner solve
 
 
 def test_simm_jordan_multiplicity(simlib):
