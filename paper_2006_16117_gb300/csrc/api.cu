@@ -441,9 +441,12 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
         P.Lcol = (const int32_t*)up("P_Lcol", Lcol.data(), sizeof(int32_t) * Lcol.size());
         P.Lidx = (const int32_t*)up("P_Lidx", Lidx.data(), sizeof(int32_t) * Lidx.size());
         P.nnzL = (int64_t)Lcol.size();
+        std::vector<int32_t> L0col(n);
+        for (int64_t g = 0; g < n; ++g) L0col[g] = Lptr[g + 1] > Lptr[g] ? Lcol[Lptr[g]] : -1;
+        P.L0col = (const int32_t*)up("P_L0col", L0col.data(), sizeof(int32_t) * L0col.size());
         SIM_CUDA(cudaStreamSynchronize(h->st));
         const size_t cs = o.precision == SIM_FP64 ? sizeof(double2) : sizeof(float2);
-        h->factor_bytes = ((size_t)2 * nb * (size_t)T * T + (size_t)P.nnzL + 16) * cs;
+        h->factor_bytes = ((size_t)2 * nb * (size_t)T * T + (size_t)P.nnzL + (size_t)n + 16) * cs;
         ensure_shift_capacity(h.get());
         h->d_f = h->arena.get<double2>("f", n);
         h->stats.n = n;

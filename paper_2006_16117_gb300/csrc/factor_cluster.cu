@@ -67,6 +67,13 @@ __global__ void __launch_bounds__(256, 1) k_factor_cl(Pencil P, const int* shift
 
     for (int64_t e = tid + (int64_t)q * blockDim.x; e < P.nnzL; e += (int64_t)blockDim.x * Cf)
         Lval[e] = from_c128<C>(sval(P, P.Lidx[e], sg));
+    {
+        C* L0val = Dinv + factor_l0_offset(P);
+        for (int64_t g = tid + (int64_t)q * blockDim.x; g < P.n; g += (int64_t)blockDim.x * Cf) {
+            const int e0 = P.Lptr[g];
+            L0val[g] = from_c128<C>(P.Lptr[g + 1] > e0 ? sval(P, P.Lidx[e0], sg) : make_double2(0.0, 0.0));
+        }
+    }
     cl.sync();
 
     for (int k = 0; k < nb; ++k) {

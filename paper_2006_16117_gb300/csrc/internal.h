@@ -41,10 +41,15 @@ struct Pencil {
     const int32_t* Lcol = nullptr;
     const int32_t* Lidx = nullptr;
     int64_t nnzL = 0;
+    // per row g: Lcol of its first coupling, -1 if it has none (a solve can
+    // load it, and the shift's first value L0val[g], without reading Lptr first)
+    const int32_t* L0col = nullptr;
 };
 
 // Offset (in elements of the factor type) of Lval inside a shift's factor.
 __host__ __device__ inline size_t factor_lval_offset(const Pencil& P) { return (size_t)2 * P.nb * P.T * P.T; }
+// Offset of L0val (n values: the first coupling's shifted value of each row, 0 if none).
+__host__ __device__ inline size_t factor_l0_offset(const Pencil& P) { return factor_lval_offset(P) + (size_t)P.nnzL; }
 
 // Workspace of a batch of Krylov jobs (one job = one Arnoldi process for
 // one shift and one starting vector).  All vectors are complex128 of length n,

@@ -65,6 +65,11 @@ __global__ void __launch_bounds__(FACTOR_THREADS) k_factor(Pencil P, const int* 
     {
         C* Lval = Dinv + factor_lval_offset(P);
         for (int64_t e = tid; e < P.nnzL; e += bd) Lval[e] = from_c128<C>(shifted_val(P, P.Lidx[e], sg));
+        C* L0val = Dinv + factor_l0_offset(P);
+        for (int64_t g = tid; g < P.n; g += bd) {
+            const int e0 = P.Lptr[g];
+            L0val[g] = P.Lptr[g + 1] > e0 ? from_c128<C>(shifted_val(P, P.Lidx[e0], sg)) : czero<C>();
+        }
     }
     for (int k = 0; k < nb; ++k) {
         C* D = Dinv + (size_t)k * TT;

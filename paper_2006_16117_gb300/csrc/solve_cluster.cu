@@ -5,19 +5,23 @@
 //   forward   t_k = Dinv_k (r_k - L_k t_{k-1}),
 //   backward  x_k = t_k - E_k x_{k+1},
 // and only the vectors depend on the previous step — the matrices do not.  So
-// each CTA of a cluster owns a slice of rows of every block and streams its
-// slices, in chain order, through a ring of shared-memory stages with 1-D TMA
-// bulk copies (cp.async.bulk + mbarrier), as far ahead as the ring allows.  The
-// per-step work is then a GEMV out of shared memory; the CTA broadcasts its
-// rows of the new vector to every CTA of the cluster through distributed
-// shared memory and one cluster barrier closes the step.  Up to R right-hand
-// sides of the same shift share each pass over the matrices (the k random
-// vectors of the multiplicity step).
+// each CTA of a cluster owns a slice of rows of every block, and a producer
+// warp streams the slices, in chain order, through a ring of shared-memory
+// stages (one 1-D bulk copy per row into a padded row, completing on the
+// stage's "full" mbarrier) as far ahead as the ring allows; the consumers
+// release a stage on its "empty" mbarrier.  Per step the eight consumer warps
+// form the right-hand side, then for each chunk of rows run the GEMV with one
+// row per lane (or a row per group of lanes) and a column range per warp, sum
+// the warps' partials through shared memory, and send the new rows of the
+// vector into every CTA's shared memory with st.async, which completes on the
+// receiver's per-step mbarrier.  Up to R right-hand sides of the same shift
+// share each pass over the matrices (the k random vectors of the
+// multiplicity step).
 //
-// Every wait on an mbarrier has an iteration limit; a CTA whose wait runs out
-// records an error, stops computing and issuing copies, keeps taking part in
-// the cluster barriers (so no CTA waits forever), and waits (again bounded)
-// for its own copies in flight before it exits.
+// Every wait on an mbarrier has an iteration limit; a thread whose wait runs
+// out records an error and the CTA stops computing and issuing copies, keeps
+// taking part in its barriers (so no thread waits forever), and waits (again
+// bounded) for its own copies in flight before it exits.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -131,28 +135,70 @@ template <> __device__ __forceinline__ float2 zero_c<float2>() { return make_flo
 
 }  // namespace
 
+// 16 bytes of complex values: two complex64 or one complex128
+template <class C> struct Vec16;
+template <> struct Vec16<float2> {
+    using T = float4;
+    static constexpr int N = 2;
+    __device__ static __forceinline__ float2 get(const float4& v, int e) {
+        return e == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+    }
+};
+template <> struct Vec16<double2> {
+    using T = double2;
+    static constexpr int N = 1;
+    __device__ static __forceinline__ double2 get(const double2& v, int) { return v; }
+};
+
+constexpr int CL_WARPS = 8;                       // consumer warps: the GEMVs and the vector work
+constexpr int CL_THREADS = (CL_WARPS + 1) * 32;   // + one producer warp that issues the copies
+
+// barrier of the consumer warps only (the producer warp never joins it)
+__device__ __forceinline__ void consumer_sync() {
+    static_assert(CL_WARPS * 32 == 256, "named barrier thread count");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool failed_flag(const int* f) { return *(const volatile int*)f != 0; }
+
 template <class C, int R>
-__global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js, int in_slot, int out_slot,
-                                                        const double2* sigma, void* const* fptrs,
-                                                        const int* grp_jobs, int SR, int NS, int* err) {
+__global__ void __launch_bounds__(CL_THREADS, 1) k_block_solve_cl(Pencil P, JobSpace js, int in_slot, int out_slot,
+                                                               void* const* fptrs, const int* grp_jobs, int SR,
+                                                               int NS, int TP, int* err) {
     cg::cluster_group cl = cg::this_cluster();
     const int Ccl = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
     const int grp = blockIdx.x / Ccl;
     const int T = P.T, nb = P.nb;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    using VT = typename Vec16<C>::T;
+    constexpr int VN = Vec16<C>::N;
+    using Rt = decltype(zero_c<C>().x);
 
-    int jb[R];
+    // the group's job vectors (in shared memory: indexed by runtime job numbers)
+    __shared__ const double2* s_in[R];
+    __shared__ double2* s_out[R];
+    __shared__ int s_fail;
     int nr = 0;
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        jb[j] = grp_jobs[grp * R + j];
-        if (jb[j] >= 0) nr = j + 1;
+    for (int j = 0; j < R; ++j)
+        if (grp_jobs[grp * R + j] >= 0) nr = j + 1;
+    const int job0 = grp_jobs[grp * R];
+    if (tid < R) {
+        const int jb = grp_jobs[grp * R + tid];
+        const int jj = jb >= 0 ? jb : job0;
+        s_in[tid] = js.vec + (size_t)jj * js.vstride + (size_t)in_slot * js.n;
+        s_out[tid] = js.vec + (size_t)jj * js.vstride + (size_t)out_slot * js.n;
     }
-    const int s = js.d_jobshift[jb[0]];
+    const int s = js.d_jobshift[job0];
     const C* Dinv = reinterpret_cast<const C*>(fptrs[s]);
     const C* E = Dinv + (size_t)nb * T * T;
     const C* Lval = Dinv + factor_lval_offset(P);
+    const C* L0val = Dinv + factor_l0_offset(P);
 
     const int Tc = (T + Ccl - 1) / Ccl;
     const int r0 = min(T, q * Tc), r1 = min(T, r0 + Tc);
@@ -161,287 +207,339 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
     const int total = (2 * nb - 1) * nsub;
 
     extern __shared__ __align__(128) unsigned char raw[];
-    C* stage = reinterpret_cast<C*>(raw);                       // [NS][SR*T]
-    C* vbuf = stage + (size_t)NS * SR * T;                      // [3][R][T]: the chain's vectors
-    C* sbuf = vbuf + (size_t)3 * R * T;                         // [R][T]
-    C* tbuf = sbuf + (size_t)R * T;                              // [R][T]: t_k rows of this CTA (backward)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tbuf + (size_t)R * T);  // [NS] stage barriers
-    uint64_t* vbar = bars + NS;                                           // [3] vector barriers
-    __shared__ int s_fail;
-
-    auto chunk_src = [&](int c, uint32_t& bytes) -> const C* {
-        const int b = c / nsub, sub = c % nsub;
-        const int rs = r0 + sub * SR;
-        const int rows = min(SR, r1 - rs);
-        bytes = (uint32_t)((size_t)rows * T * sizeof(C));
-        const C* M = b < nb ? Dinv + (size_t)b * T * T : E + (size_t)(2 * nb - 2 - b) * T * T;
-        return M + (size_t)rs * T;
-    };
+    C* stage = reinterpret_cast<C*>(raw);                  // [NS][SR][TP]: rows padded to TP
+    C* vbuf = stage + (size_t)NS * SR * TP;                // [3][R][T]: the chain's vectors
+    C* sbuf = vbuf + (size_t)3 * R * T;                    // [R][T]
+    C* tbuf = sbuf + (size_t)R * T;                        // [R][T]: t_k rows of this CTA (backward)
+    C* red = tbuf + (size_t)R * T;                         // [2][warps][R][SR]: per-warp partial sums
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)2 * CL_WARPS * R * SR);  // [NS] stage filled
+    uint64_t* empty = full + NS;                                                         // [NS] stage consumed
+    uint64_t* vbar = empty + NS;                                                         // [3] vector received
 
     if (tid == 0) {
         s_fail = 0;
-        for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
         for (int i = 0; i < 3; ++i) mbar_init(&vbar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int issued = 0;
-    if (tid == 0) {
-        for (; issued < min(NS, total); ++issued) {
-            uint32_t bytes;
-            const C* src = chunk_src(issued, bytes);
-            mbar_expect_tx(&bars[issued], bytes);
-            tma_load_1d(stage + (size_t)issued * SR * T, src, bytes, &bars[issued]);
-        }
-    }
     const uint32_t vec_bytes = (uint32_t)((size_t)T * nr * sizeof(C));  // one step's vector, all rows
     if (tid == 0)
         for (int i = 0; i < 3 && i <= 2 * nb - 3; ++i) mbar_expect_tx(&vbar[i], vec_bytes);  // steps 0, 1, 2
     cl.sync();  // every CTA of the cluster is running, barriers initialised and armed, before any remote store
 
-    const double2* in[R];
-    double2* out[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int jj = jb[j] >= 0 ? jb[j] : jb[0];
-        in[j] = js.vec + (size_t)jj * js.vstride + (size_t)in_slot * js.n;
-        out[j] = js.vec + (size_t)jj * js.vstride + (size_t)out_slot * js.n;
-    }
-
-    // Register prefetch of the next step's chain-independent inputs: r_k and
-    // the first coupling of each row (forward), t_k of this CTA's rows (backward).
-    constexpr int PFN = 8;
-    const bool pf_ok = T * nr <= PFN * (int)blockDim.x;
-    C pf_v[PFN], pf_a[PFN];
-    int pf_c[PFN], pf_n[PFN];
-    auto prefetch_fwd = [&](int kk) {
-        const int64_t gg0 = (int64_t)kk * T;
-#pragma unroll
-        for (int t = 0; t < PFN; ++t) {
-            const int idx = tid + t * (int)blockDim.x;
-            pf_n[t] = -1;
-            if (idx < T * nr) {
-                const int i = idx % T, j = idx / T;
-                const int64_t g = gg0 + i;
-                if (g < P.n) {
-                    pf_v[t] = from_c128<C>(in[j][g]);
-                    const int e0 = P.Lptr[g], e1 = P.Lptr[g + 1];
-                    pf_n[t] = e1 - e0;
-                    if (e1 > e0) {
-                        pf_c[t] = P.Lcol[e0];
-                        pf_a[t] = Lval[e0];
-                    }
-                } else {
-                    pf_n[t] = -2;
-                }
-            }
-        }
-    };
-    auto prefetch_bwd = [&](int kk) {
-        const int64_t gg0 = (int64_t)kk * T + r0;
-#pragma unroll
-        for (int t = 0; t < PFN; ++t) {
-            const int idx = tid + t * (int)blockDim.x;
-            pf_n[t] = -1;
-            if (idx < myrows * nr) {
-                const int i = idx % myrows, j = idx / myrows;
-                const int64_t g = gg0 + i;
-                pf_v[t] = g < P.n ? from_c128<C>(out[j][g]) : zero_c<C>();
-                pf_n[t] = 0;
-            }
-        }
-    };
-    const bool pfb_ok = myrows * nr <= PFN * (int)blockDim.x;
-    if (pf_ok) prefetch_fwd(0);
-
-    int chunk = 0;
-    for (int b = 0; b < 2 * nb - 1; ++b) {
-        const bool fwd = b < nb;
-        const int k = fwd ? b : 2 * nb - 2 - b;
-        const int64_t g0 = (int64_t)k * T;
-        const int cur = b % 3, prv = (b + 2) % 3;
-        const C* vprev = vbuf + (size_t)prv * R * T;  // t_{k-1} (fwd) or x_{k+1} (bwd)
-        const bool last = b == 2 * nb - 2;            // nobody reads the last vector: not sent
-        if (b > 0 && !s_fail) {
-            // the previous step's vector: every CTA's rows, delivered by st.async
-            const uint32_t par = (uint32_t)(((b - 1) / 3) & 1);
-            long long it = 0;
-            while (!mbar_try_wait_cluster(&vbar[prv], par)) {
-                if (++it > WAIT_LIMIT) {
-                    s_fail = 1;
-                    atomicExch(err, 3);
-                    break;
-                }
-            }
-        }
-        __syncthreads();
-        // re-arm that barrier for step b+2 now: no CTA can send step b+2's rows
-        // before it has ours of step b+1, so the expected bytes are always
-        // registered before the first of them arrives
-        if (tid == 0 && b > 0 && !s_fail && b + 2 <= 2 * nb - 3) mbar_expect_tx(&vbar[prv], vec_bytes);
-        const bool failed = s_fail != 0;
-        if (fwd && !failed && pf_ok) {
-            // s_k = r_k - L_k t_{k-1}: every CTA forms the whole block
-#pragma unroll
-            for (int t = 0; t < PFN; ++t) {
-                const int idx = tid + t * (int)blockDim.x;
-                if (idx >= T * nr) break;
-                const int i = idx % T, j = idx / T;
-                C v = zero_c<C>();
-                if (pf_n[t] >= 0) {
-                    v = pf_v[t];
-                    if (pf_n[t] >= 1) {
-                        const C a = pf_a[t];
-                        const C tt = vprev[(size_t)j * T + pf_c[t]];
-                        v.x -= a.x * tt.x - a.y * tt.y;
-                        v.y -= a.x * tt.y + a.y * tt.x;
-                    }
-                    if (pf_n[t] > 1) {
-                        const int64_t g = g0 + i;
-                        for (int e = P.Lptr[g] + 1; e < P.Lptr[g + 1]; ++e) {
-                            const C a = Lval[e];
-                            const C tt = vprev[(size_t)j * T + P.Lcol[e]];
-                            v.x -= a.x * tt.x - a.y * tt.y;
-                            v.y -= a.x * tt.y + a.y * tt.x;
+    if (warp == CL_WARPS) {
+        // ---- producer: chunk c = up to SR rows of one block, one 1-D bulk copy
+        // per row into its padded row of stage c % NS, once that stage is consumed
+        int c = 0;
+        for (; c < total; ++c) {
+            const int slot = c % NS;
+            int ok = 1;
+            if (lane == 0) {
+                if (c >= NS) {
+                    const uint32_t par = (uint32_t)(((c / NS) - 1) & 1);
+                    long long it = 0;
+                    while (!mbar_try_wait(&empty[slot], par)) {
+                        if (failed_flag(&s_fail)) {
+                            ok = 0;
+                            break;
+                        }
+                        if (++it > WAIT_LIMIT) {
+                            s_fail = 1;
+                            atomicExch(err, 4);
+                            ok = 0;
+                            break;
                         }
                     }
                 }
-                sbuf[(size_t)j * T + i] = v;
+                if (failed_flag(&s_fail)) ok = 0;
             }
-            __syncthreads();
-            if (k + 1 < nb) prefetch_fwd(k + 1);
-            else if (pfb_ok) prefetch_bwd(nb - 2 >= 0 ? nb - 2 : 0);
-        } else if (fwd && !failed) {
-            for (int idx = tid; idx < T * nr; idx += blockDim.x) {
-                const int i = idx % T, j = idx / T;
-                const int64_t g = g0 + i;
-                C v = zero_c<C>();
-                if (g < P.n) {
-                    v = from_c128<C>(in[j][g]);
-                    const int e0 = P.Lptr[g], e1 = P.Lptr[g + 1];
-                    for (int e = e0; e < e1; ++e) {
-                        const C a = Lval[e];
-                        const C t = vprev[(size_t)j * T + P.Lcol[e]];
-                        v.x -= a.x * t.x - a.y * t.y;
-                        v.y -= a.x * t.y + a.y * t.x;
-                    }
-                }
-                sbuf[(size_t)j * T + i] = v;
-            }
-            __syncthreads();
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            const int b = c / nsub, sub = c % nsub;
+            const int rs = r0 + sub * SR;
+            const int rows = min(SR, r1 - rs);
+            const C* M = (b < nb ? Dinv + (size_t)b * T * T : E + (size_t)(2 * nb - 2 - b) * T * T) + (size_t)rs * T;
+            C* dst = stage + (size_t)slot * SR * TP;
+            if (lane == 0) mbar_expect_tx(&full[slot], (uint32_t)((size_t)rows * T * sizeof(C)));
+            __syncwarp();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int i = lane; i < rows; i += 32)
+                tma_load_1d(dst + (size_t)i * TP, M + (size_t)i * T, (uint32_t)(T * sizeof(C)), &full[slot]);
         }
-        const C* rhs = fwd ? sbuf : vprev;
-        if (!fwd && !failed) {
-            // t_k of this CTA's rows, for x_k = t_k - E_k x_{k+1}
-            if (pfb_ok) {
-#pragma unroll
-                for (int t = 0; t < PFN; ++t) {
-                    const int idx = tid + t * (int)blockDim.x;
-                    if (idx < myrows * nr) tbuf[(size_t)(idx / myrows) * T + idx % myrows] = pf_v[t];
-                }
-                if (k > 0) prefetch_bwd(k - 1);
-            } else {
-                for (int idx = tid; idx < myrows * nr; idx += blockDim.x) {
-                    const int i = idx % myrows, j = idx / myrows;
-                    const int64_t g = g0 + r0 + i;
-                    tbuf[(size_t)j * T + i] = g < P.n ? from_c128<C>(out[j][g]) : zero_c<C>();
-                }
-            }
-        }
-        for (int sub = 0; sub < nsub; ++sub, ++chunk) {
-            const int slot = chunk % NS;
-            if (!s_fail) {
-                const uint32_t par = (uint32_t)((chunk / NS) & 1);
+        // stopped early (a failure): the last issued copies may still be in flight,
+        // and this CTA's shared memory must outlive them
+        if (lane == 0 && c < total) {
+            for (int d = max(0, c - NS); d < c; ++d) {
                 long long it = 0;
-                while (!mbar_try_wait(&bars[slot], par)) {
+                while (!mbar_try_wait(&full[d % NS], (uint32_t)((d / NS) & 1)) && ++it < WAIT_LIMIT) {
+                }
+            }
+        }
+    } else {
+        // ---- consumers
+        // Prefetch of the next step's chain-independent inputs, one row per
+        // thread, kept as loaded (no arithmetic on them until they are used):
+        // r_k and the row's couplings (forward), t_k of this CTA's rows (backward).
+        const bool pf_ok = T <= CL_WARPS * 32;
+        double2 pf_v[R];
+        int pf_lo = 0, pf_hi = 0, pf_c = 0;
+        C pf_a = zero_c<C>();
+        auto prefetch_fwd = [&](int kk) {
+            const int64_t g = (int64_t)kk * T + tid;
+            if (tid < T) {
+                const bool in = g < P.n;
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (j < nr) pf_v[j] = in ? s_in[j][g] : make_double2(0.0, 0.0);
+                if (in) {
+                    pf_lo = P.Lptr[g];
+                    pf_hi = P.Lptr[g + 1];
+                    pf_c = P.L0col[g];
+                    pf_a = L0val[g];
+                } else {
+                    pf_lo = pf_hi = 0;
+                }
+            }
+        };
+        auto prefetch_bwd = [&](int kk) {
+            const int64_t g = (int64_t)kk * T + r0 + tid;
+            if (tid < myrows) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (j < nr) pf_v[j] = g < P.n ? s_out[j][g] : make_double2(0.0, 0.0);
+            }
+        };
+        if (pf_ok) prefetch_fwd(0);
+
+        // this warp's 16-byte column units of every row
+        const int U = T / VN;
+        const int u0 = (warp * U) / CL_WARPS, u1 = ((warp + 1) * U) / CL_WARPS;
+
+        int chunk = 0;
+        for (int b = 0; b < 2 * nb - 1; ++b) {
+            const bool fwd = b < nb;
+            const int k = fwd ? b : 2 * nb - 2 - b;
+            const int64_t g0 = (int64_t)k * T;
+            const int cur = b % 3, prv = (b + 2) % 3;
+            const C* vprev = vbuf + (size_t)prv * R * T;  // t_{k-1} (fwd) or x_{k+1} (bwd)
+            const bool last = b == 2 * nb - 2;            // nobody reads the last vector: not sent
+            if (b > 0 && !failed_flag(&s_fail)) {
+                // the previous step's vector: every CTA's rows, delivered by st.async
+                const uint32_t par = (uint32_t)(((b - 1) / 3) & 1);
+                long long it = 0;
+                while (!mbar_try_wait_cluster(&vbar[prv], par)) {
+                    if (failed_flag(&s_fail)) break;
                     if (++it > WAIT_LIMIT) {
                         s_fail = 1;
-                        atomicExch(err, 2);
+                        atomicExch(err, 3);
                         break;
                     }
                 }
             }
-            __syncthreads();
-            if (!s_fail) {
-                const C* M = stage + (size_t)slot * SR * T;
+            consumer_sync();  // also: the previous step's reads of sbuf and tbuf are done
+            // re-arm that barrier for step b+2 now: no CTA can send step b+2's rows
+            // before it has ours of step b+1, so the expected bytes are always
+            // registered before the first of them arrives
+            if (tid == 0 && b > 0 && !failed_flag(&s_fail) && b + 2 <= 2 * nb - 3)
+                mbar_expect_tx(&vbar[prv], vec_bytes);
+            const bool failed = failed_flag(&s_fail);
+            if (fwd) {
+                // s_k = r_k - L_k t_{k-1}: every CTA forms the whole block
+                if (failed) {
+                } else if (pf_ok) {
+                    if (tid < T) {
+                        const int i = tid;
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            if (j >= nr) break;
+                            C v = from_c128<C>(pf_v[j]);
+                            if (pf_hi > pf_lo) {
+                                const C tt = vprev[(size_t)j * T + pf_c];
+                                v.x -= pf_a.x * tt.x - pf_a.y * tt.y;
+                                v.y -= pf_a.x * tt.y + pf_a.y * tt.x;
+                                for (int e = pf_lo + 1; e < pf_hi; ++e) {
+                                    const C a = Lval[e];
+                                    const C t2 = vprev[(size_t)j * T + P.Lcol[e]];
+                                    v.x -= a.x * t2.x - a.y * t2.y;
+                                    v.y -= a.x * t2.y + a.y * t2.x;
+                                }
+                            }
+                            sbuf[(size_t)j * T + i] = v;
+                        }
+                    }
+                    if (k + 1 < nb) prefetch_fwd(k + 1);
+                    else prefetch_bwd(nb - 2 >= 0 ? nb - 2 : 0);
+                } else {
+                    for (int idx = tid; idx < T * nr; idx += CL_WARPS * 32) {
+                        const int i = idx % T, j = idx / T;
+                        const int64_t g = g0 + i;
+                        C v = zero_c<C>();
+                        if (g < P.n) {
+                            v = from_c128<C>(s_in[j][g]);
+                            const int e0 = P.Lptr[g], e1 = P.Lptr[g + 1];
+                            for (int e = e0; e < e1; ++e) {
+                                const C a = Lval[e];
+                                const C t = vprev[(size_t)j * T + P.Lcol[e]];
+                                v.x -= a.x * t.x - a.y * t.y;
+                                v.y -= a.x * t.y + a.y * t.x;
+                            }
+                        }
+                        sbuf[(size_t)j * T + i] = v;
+                    }
+                }
+                consumer_sync();
+            }
+            const C* rhs = fwd ? sbuf : vprev;
+            if (!fwd && !failed) {
+                // t_k of this CTA's rows, for x_k = t_k - E_k x_{k+1} (read after the next barrier)
+                if (pf_ok) {
+                    if (tid < myrows) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j)
+                            if (j < nr) tbuf[(size_t)j * T + tid] = from_c128<C>(pf_v[j]);
+                    }
+                    if (k > 0) prefetch_bwd(k - 1);
+                } else {
+                    for (int idx = tid; idx < myrows * nr; idx += CL_WARPS * 32) {
+                        const int i = idx % myrows, j = idx / myrows;
+                        const int64_t g = g0 + r0 + i;
+                        tbuf[(size_t)j * T + i] = g < P.n ? from_c128<C>(s_out[j][g]) : zero_c<C>();
+                    }
+                }
+            }
+            for (int sub = 0; sub < nsub; ++sub, ++chunk) {
+                const int slot = chunk % NS;
+                C* rbuf = red + (size_t)(chunk & 1) * CL_WARPS * R * SR;
+                if (!failed_flag(&s_fail)) {
+                    const uint32_t par = (uint32_t)((chunk / NS) & 1);
+                    long long it = 0;
+                    while (!mbar_try_wait(&full[slot], par)) {
+                        if (failed_flag(&s_fail)) break;
+                        if (++it > WAIT_LIMIT) {
+                            s_fail = 1;
+                            atomicExch(err, 2);
+                            break;
+                        }
+                    }
+                }
                 const int rs = r0 + sub * SR;
                 const int rows = min(SR, r1 - rs);
-                constexpr int RP = R == 1 ? 4 : (R == 2 ? 2 : 1);  // rows per warp pass
-                constexpr int NSC = 2 * RP * R;                      // real accumulators per lane
-                constexpr int LOGS = NSC == 16 ? 4 : 3;
-                constexpr int SH = 5 - LOGS;                         // lane bits below the value index
-                using Rt = decltype(zero_c<C>().x);
-                for (int rb = warp * RP; rb < rows; rb += nw * RP) {
-                    Rt acc[NSC];
+                // warp-uniform test: the GEMV's shuffles need every lane, and the
+                // flag can change under a warp's feet (the producer sets it too)
+                if (__all_sync(0xffffffffu, !failed_flag(&s_fail))) {
+                    // lane = row r (of SRp, the power of two >= rows) + SRp * column phase cp
+                    int lg = 0;
+                    while ((1 << lg) < rows) ++lg;
+                    const int SRp = 1 << lg;
+                    const int CP = 32 >> lg;
+                    const int r = lane & (SRp - 1), cp = lane >> lg;
+                    Rt acc[2 * R];
 #pragma unroll
-                    for (int u = 0; u < NSC; ++u) acc[u] = Rt(0);
-                    for (int c = lane; c < T; c += 32) {
-                        C xv[R];
+                    for (int v = 0; v < 2 * R; ++v) acc[v] = Rt(0);
+                    auto mac = [&](const VT& mv, const VT (&xv)[R]) {
 #pragma unroll
-                        for (int j = 0; j < R; ++j) xv[j] = rhs[(size_t)j * T + c];  // consecutive across lanes
+                        for (int j = 0; j < R; ++j) {
 #pragma unroll
-                        for (int p = 0; p < RP; ++p) {
-                            if (rb + p < rows) {
-                                const C m = M[(size_t)(rb + p) * T + c];
+                            for (int e = 0; e < VN; ++e) {
+                                const C m = Vec16<C>::get(mv, e), x = Vec16<C>::get(xv[j], e);
+                                acc[2 * j] = fma(m.x, x.x, acc[2 * j]);
+                                acc[2 * j] = fma(-m.y, x.y, acc[2 * j]);
+                                acc[2 * j + 1] = fma(m.x, x.y, acc[2 * j + 1]);
+                                acc[2 * j + 1] = fma(m.y, x.x, acc[2 * j + 1]);
+                            }
+                        }
+                    };
+                    if (r < rows) {
+                        const VT* Mrow = reinterpret_cast<const VT*>(stage + ((size_t)slot * SR + r) * TP);
+                        const VT* X = reinterpret_cast<const VT*>(rhs);  // unit u of job j at X[j * U + u]
+                        int u = u0 + cp;
+                        if constexpr (sizeof(C) == 8) {
+                            // complex64: the next unit's operands load while this one's FMAs run
+                            if (u < u1) {
+                                VT mv = Mrow[u];
+                                VT xv[R];
 #pragma unroll
-                                for (int j = 0; j < R; ++j) {
-                                    Rt& re = acc[(p * R + j) * 2];
-                                    Rt& im = acc[(p * R + j) * 2 + 1];
-                                    re = fma(m.x, xv[j].x, re);
-                                    re = fma(-m.y, xv[j].y, re);
-                                    im = fma(m.x, xv[j].y, im);
-                                    im = fma(m.y, xv[j].x, im);
+                                for (int j = 0; j < R; ++j) xv[j] = X[(size_t)j * U + u];
+                                while (true) {
+                                    const int un = u + CP;
+                                    const bool more = un < u1;
+                                    VT mn = mv;
+                                    VT xn[R];
+#pragma unroll
+                                    for (int j = 0; j < R; ++j) xn[j] = xv[j];
+                                    if (more) {
+                                        mn = Mrow[un];
+#pragma unroll
+                                        for (int j = 0; j < R; ++j) xn[j] = X[(size_t)j * U + un];
+                                    }
+                                    mac(mv, xv);
+                                    if (!more) break;
+                                    mv = mn;
+#pragma unroll
+                                    for (int j = 0; j < R; ++j) xv[j] = xn[j];
+                                    u = un;
                                 }
+                            }
+                        } else {
+                            for (; u < u1; u += CP) {
+                                const VT mv = Mrow[u];
+                                VT xv[R];
+#pragma unroll
+                                for (int j = 0; j < R; ++j) xv[j] = X[(size_t)j * U + u];
+                                mac(mv, xv);
                             }
                         }
                     }
-                    // butterfly: NSC sums over the warp with NSC shuffles in all;
-                    // lane L ends with the sum of value (L >> SH) & (NSC - 1)
-                    butterfly<Rt, NSC>(acc, lane);
-                    const Rt mine = acc[0];
-                    const Rt other = __shfl_xor_sync(0xffffffffu, mine, 1 << SH);
-                    const int kv = (lane >> SH) & (NSC - 1);
-                    if ((lane & ((1 << SH) - 1)) == 0 && (kv & 1) == 0) {
-                        const int pair = kv >> 1;
-                        const int p = pair / R, j = pair % R;
-                        if (rb + p < rows && j < nr) {
-                            const int r = rs + rb + p;
-                            const int64_t g = g0 + r;
-                            C val;
-                            val.x = mine;
-                            val.y = other;
-                            if (!fwd) val = csub(tbuf[(size_t)j * T + (r - r0)], val);
-                            if (g < P.n) out[j][g] = to_c128(val);
-                            if (!last) {
-                                C* loc = vbuf + (size_t)cur * R * T + (size_t)j * T + r;
-                                for (int qq = 0; qq < Ccl; ++qq)
-                                    st_async_c(mapa_u32(loc, qq), val, mapa_u32(&vbar[cur], qq));
+                    // sum the column phases of each row
+                    for (int mask = 16; mask >= SRp; mask >>= 1) {
+#pragma unroll
+                        for (int v = 0; v < 2 * R; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], mask);
+                    }
+                    if (cp == 0 && r < rows) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            if (j < nr) {
+                                C v;
+                                v.x = acc[2 * j];
+                                v.y = acc[2 * j + 1];
+                                rbuf[((size_t)warp * R + j) * SR + r] = v;
                             }
                         }
                     }
                 }
-            }
-            __syncthreads();  // the stage is consumed
-            if (tid == 0 && !s_fail && issued < total) {
-                uint32_t bytes;
-                const C* src = chunk_src(issued, bytes);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&bars[issued % NS], bytes);
-                tma_load_1d(stage + (size_t)(issued % NS) * SR * T, src, bytes, &bars[issued % NS]);
-                ++issued;
+                consumer_sync();  // partial sums written; the stage is consumed
+                if (tid == 0) mbar_arrive(&empty[slot]);
+                if (!failed_flag(&s_fail)) {
+                    // one thread per (row, job): sum the warps' partials, store, broadcast
+                    for (int t = tid; t < rows * nr; t += CL_WARPS * 32) {
+                        const int r = t % rows, j = t / rows;
+                        C v = rbuf[(size_t)j * SR + r];
+#pragma unroll
+                        for (int w = 1; w < CL_WARPS; ++w) {
+                            const C p = rbuf[((size_t)w * R + j) * SR + r];
+                            v.x += p.x;
+                            v.y += p.y;
+                        }
+                        const int rr = rs + r;
+                        const int64_t g = g0 + rr;
+                        if (!fwd) v = csub(tbuf[(size_t)j * T + (rr - r0)], v);
+                        if (g < P.n) s_out[j][g] = to_c128(v);
+                        if (!last) {
+                            C* loc = vbuf + (size_t)cur * R * T + (size_t)j * T + rr;
+                            for (int qq = 0; qq < Ccl; ++qq)
+                                st_async_c(mapa_u32(loc, qq), v, mapa_u32(&vbar[cur], qq));
+                        }
+                    }
+                }
             }
         }
     }
-    // a failed CTA still has copies in flight: wait for them (bounded) before exit;
-    // the final cluster barrier keeps every CTA's shared memory alive until all
-    // peers have finished
-    if (tid == 0 && s_fail) {
-        for (int c = chunk; c < issued; ++c) {
-            long long it = 0;
-            while (!mbar_try_wait(&bars[c % NS], (uint32_t)((c / NS) & 1)) && ++it < WAIT_LIMIT) {
-            }
-        }
-    }
+    // the cluster barrier keeps every CTA's shared memory alive until all peers
+    // have finished sending into it
     cl.sync();
 }
 
@@ -449,33 +547,77 @@ __global__ void __launch_bounds__(256, 1) k_block_solve_cl(Pencil P, JobSpace js
 namespace {
 
 struct Plan {
-    int R = 1, SR = 1, NS = 3;
+    int R = 1, SR = 1, NS = 3, TP = 1;
     size_t smem = 0;
 };
 
+// Row stride (complex values) of a stage in shared memory: a whole number of
+// 16-byte units, and an odd one, so that the 16-byte loads of 8 consecutive
+// rows at the same column fall in distinct bank groups.
+int padded_row(int T, size_t cs) {
+    int TP = T;
+    while ((TP * cs) % 16 != 0 || ((TP * cs / 16) & 1) == 0) ++TP;
+    return TP;
+}
+
+size_t plan_smem(const Plan& p, int T, size_t cs) {
+    return (size_t)p.NS * p.SR * p.TP * cs + (size_t)5 * p.R * T * cs + (size_t)2 * CL_WARPS * p.R * p.SR * cs +
+           (2 * p.NS + 3) * sizeof(uint64_t) + 16;
+}
+
+// Largest R (right-hand sides per pass) and stage height SR that fit.
 bool make_plan(int T, size_t cs, int want_R, Plan& p) {
     const size_t budget = 220 * 1024;
+    const int TP = padded_row(T, cs);
     for (int R : {8, 4, 2, 1}) {
         if (R > want_R && R != 1) continue;
         const size_t vec = (size_t)5 * R * T * cs;
-        if (vec + 64 >= budget) continue;
+        if (vec + 96 >= budget) continue;
         const int NS = 3;
-        const size_t per_row = (size_t)NS * T * cs;
-        int SR = (int)std::min<size_t>(32, (budget - vec - 64) / per_row);
+        const size_t per_row = (size_t)NS * TP * cs + (size_t)2 * CL_WARPS * R * cs;
+        const int SR = (int)std::min<size_t>(32, (budget - vec - 96) / per_row);
         if (SR < 1) continue;
         p.R = R;
         p.SR = SR;
         p.NS = NS;
-        p.smem = (size_t)NS * SR * T * cs + vec + (NS + 3) * sizeof(uint64_t) + 16;
+        p.TP = TP;
+        p.smem = plan_smem(p, T, cs);
         return true;
     }
     return false;
 }
 
+// Stage height for a CTA of Tc rows: each chunk of `rows` rows occupies the
+// lanes as rows x column phases with rows padded to a power of two, so the
+// estimate charges the padded rows' multiply-adds (FP32: 4 warp-instructions
+// a clock per SM, FP64: one per 16 clocks) plus a fixed cost per chunk (its
+// waits, barrier and epilogue, about 2 us).
+int choose_rows(int Tc, int SRmax, int T, size_t cs, int R) {
+    const int VN = (int)(16 / cs);
+    const int Uw = (T / VN + CL_WARPS - 1) / CL_WARPS;
+    const double per_fma = cs == 16 ? 16.0 : 0.25;
+    int best = SRmax;
+    double best_c = 1e300;
+    for (int SR = 1; SR <= SRmax; ++SR) {
+        double c = 0.0;
+        for (int a = 0; a < Tc; a += SR) {
+            const int rows = std::min(SR, Tc - a);
+            int SRp = 1;
+            while (SRp < rows) SRp <<= 1;
+            const int CP = 32 / SRp;
+            c += (double)((Uw + CP - 1) / CP) * R * VN * 4 * CL_WARPS * per_fma + 4000.0;
+        }
+        if (c < best_c) {
+            best_c = c;
+            best = SR;
+        }
+    }
+    return best;
+}
+
 template <class C, int R>
-void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, const double2* d_sigma,
-               void* const* fptrs, const int* d_grp, int ngroups, int Ccl, const Plan& pl, int* d_err,
-               cudaStream_t st) {
+void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, void* const* fptrs, const int* d_grp,
+               int ngroups, int Ccl, const Plan& pl, int* d_err, cudaStream_t st) {
     auto kern = k_block_solve_cl<C, R>;
     static size_t attr_set = 0;  // per instantiation
     if (pl.smem > attr_set) {
@@ -484,7 +626,7 @@ void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, c
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ngroups * Ccl);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(CL_THREADS);
     cfg.dynamicSmemBytes = pl.smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -494,7 +636,7 @@ void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, c
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SIM_CUDA(cudaLaunchKernelEx(&cfg, kern, P, js, in_slot, out_slot, d_sigma, fptrs, d_grp, pl.SR, pl.NS, d_err));
+    SIM_CUDA(cudaLaunchKernelEx(&cfg, kern, P, js, in_slot, out_slot, fptrs, d_grp, pl.SR, pl.NS, pl.TP, d_err));
     SIM_LAUNCH_CHECK();
 }
 
@@ -568,16 +710,12 @@ bool block_solve_cluster(const Pencil& P, int precision, const JobSpace& js, con
     int Ccl = 8;
     while (Ccl > 1 && (int64_t)Ccl * ng > 152) Ccl >>= 1;
     Ccl = std::min(Ccl, P.T);
-    {
-        // equal chunks: a CTA's rows in as few stages-worth pieces as the ring allows
-        const int Tc = (P.T + Ccl - 1) / Ccl;
-        const int nsub = (Tc + pl.SR - 1) / pl.SR;
-        pl.SR = (Tc + nsub - 1) / nsub;
-    }
+    pl.SR = choose_rows((P.T + Ccl - 1) / Ccl, pl.SR, P.T, cs, pl.R);
+    pl.smem = plan_smem(pl, P.T, cs);
     const double TT = (double)P.T * P.T, blocks = 2.0 * P.nb - 1.0;
     kprof_begin("block_solve", st);
 #define SIM_LAUNCH_R(CT, RR) \
-    launch_cl<CT, RR>(P, js, in_slot, out_slot, d_sigma, d_factor_ptrs, d_grp, ng, Ccl, pl, g_err, st)
+    launch_cl<CT, RR>(P, js, in_slot, out_slot, d_factor_ptrs, d_grp, ng, Ccl, pl, g_err, st)
     if (precision == SIM_FP64) {
         if (pl.R == 8) SIM_LAUNCH_R(double2, 8);
         else if (pl.R == 4) SIM_LAUNCH_R(double2, 4);
