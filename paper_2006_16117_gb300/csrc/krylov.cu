@@ -24,6 +24,7 @@
 
 #include "internal.h"
 #include "levels.h"
+#include "gs.h"
 #include "solve_cluster.h"
 
 namespace sim {
@@ -375,38 +376,6 @@ __global__ void k_apply_B_jobs(Pencil P, JobSpace js, int j, int y_slot) {
 // ---------------------------------------------------------------------------
 // batched classical Gram–Schmidt, applied twice (CGS2), FP64
 // ---------------------------------------------------------------------------
-// Vectors of job `job`: basis vector i at basis + job*bstride + i*n; w at
-// w + job*wstride.  Coefficients go to hcol + job*hstride (+= for the second
-// pass), the norm to hcol[cnt].  Partial sums of one pass are written to
-// pout and read by the next kernel from pin (two buffers, since every CTA of
-// a job reads all of that job's partials).
-struct GSArgs {
-    const double2* basis;
-    int64_t bstride;
-    double2* w;
-    int64_t wstride;
-    double2* hcol;
-    int64_t hstride;
-    int cnt;
-    int64_t n;
-    const double2* pin;   // [job][chunk][pw]
-    double2* pout;
-    int pw;
-    int nchunk;
-    const int* active;
-    // Arnoldi breakdown test (optional): H base / stride / ld and column j
-    const double2* Hfull;
-    int64_t Hstride;
-    int Hld;
-    int j;
-    double btol;
-    int* meff;      // per job (optional)
-    int* istat;     // per job IS_N ints (optional): IS_BROKEN flag
-    // selective reorthogonalisation (Daniel-Gragg-Kaufman-Stewart): the second
-    // pass runs only if the first one cut the norm of w below 1/sqrt(2) of it
-    int dgks;
-};
-
 __device__ __forceinline__ void block_reduce_vec(double2* red, int cnt, int nw) {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         double2 s = red[i * nw];
@@ -596,6 +565,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_finish(GSArgs a) {
 
 // one CGS2 step on the active jobs: partial buffers A = partial, B = partial + half
 static void gs_run(GSArgs a, double2* partial, size_t half, int nactive, cudaStream_t st) {
+    if (gs_cluster(a, nactive, st)) return;
     kprof_begin("gram_schmidt", st);
     dim3 grid(a.nchunk, nactive);
     const int nw = GS_THREADS / 32;
@@ -804,6 +774,7 @@ void norm_and_scale(const JobSpace& js, int nactive, double2* w_base, int64_t ws
     a.pw = js.pw;
     a.nchunk = js.nchunk;
     a.active = js.d_active;
+    if (gs_cluster(a, nactive, st)) return;
     dim3 grid(js.nchunk, nactive);
     const int nw = GS_THREADS / 32;
     a.pout = js.partial;
