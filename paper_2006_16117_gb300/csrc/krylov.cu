@@ -328,7 +328,24 @@ __global__ void k_spmv_jobs(Pencil P, JobSpace js, int x_slot, int y_slot, int r
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= P.n) return;
     double2 acc = make_double2(0.0, 0.0);
-    for (int64_t e = P.rp[g]; e < P.rp[g + 1]; ++e) acc = cfma(shifted_val(P, e, sg), x[P.ci[e]], acc);
+    if (P.b_kind <= 1) {
+        // B = I or diagonal: A - σB differs from A on the diagonal only, so σB_gg
+        // is formed once and subtracted there (the same value shifted_val gives),
+        // by a select rather than a branch so the loads stay in flight
+        const double2 b = P.Bdiag[g];
+        const double sbx = sg.x * b.x - sg.y * b.y, sby = sg.x * b.y + sg.y * b.x;
+        const int64_t e0 = P.rp[g], e1 = P.rp[g + 1];
+#pragma unroll 4
+        for (int64_t e = e0; e < e1; ++e) {
+            const int64_t j = P.ci[e];
+            const double2 a = P.Ka[e];
+            const bool d = j == g;
+            const double2 v = make_double2(d ? a.x - sbx : a.x, d ? a.y - sby : a.y);
+            acc = cfma(v, x[j], acc);
+        }
+    } else {
+        for (int64_t e = P.rp[g]; e < P.rp[g + 1]; ++e) acc = cfma(shifted_val(P, e, sg), x[P.ci[e]], acc);
+    }
     if (rhs_slot >= 0) {
         double2 r = js.vec[(size_t)job * js.vstride + (size_t)rhs_slot * js.n + g];
         acc = csub(r, acc);
