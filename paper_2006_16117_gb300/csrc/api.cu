@@ -315,6 +315,7 @@ void sim_default_options(sim_options* o) {
     o->inner_restart = 8;
     o->inner_max_iter = 64;
     o->mult_inner_tol = 1e-10;
+    o->mult_reorth = 0;
 }
 
 sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream, sim_handle* out) {
@@ -331,7 +332,7 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
             o.mult_kmax < o.mult_k || o.mult_kmax > 64 || o.mult_nodes < 4 || o.mult_nodes > 64 ||
             !(o.inner_tol > 0) || !(o.mult_inner_tol > 0) || o.inner_restart < 1 || o.inner_restart > 32 || o.inner_max_iter < 1 ||
             (o.precision != SIM_FP64 && o.precision != SIM_MIXED) || o.max_squares < 1 ||
-            (o.residual_scale != 0 && o.residual_scale != 1))
+            (o.residual_scale != 0 && o.residual_scale != 1) || (o.mult_reorth != 0 && o.mult_reorth != 1))
             return fail(nullptr, SIM_ERR_INVALID_ARG, "options out of range (m must be <= 52, n0 must be 4)");
         HostCsr a, b;
         std::string why;

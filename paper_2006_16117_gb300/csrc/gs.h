@@ -35,6 +35,8 @@ struct GSArgs {
     // selective reorthogonalisation (Daniel-Gragg-Kaufman-Stewart): the second
     // pass runs only if the first one cut the norm of w below 1/sqrt(2) of it
     int dgks;
+    // one pass only (the classical Gram-Schmidt printed in Sec. 2); overrides dgks
+    int single;
 };
 
 // The whole CGS2 step of gs_run in one cluster launch per call (gs_cluster.cu):

@@ -141,11 +141,11 @@ __global__ void __launch_bounds__(GC_THREADS, 2) k_gs_cluster(GSArgs a) {
         for (int i = tid; i < cnt; i += GC_THREADS) S.h1[i] = S.tot[i];
         update();
         // the barriers in cluster_sum order S.h1's writes before its reads below
-        bool second = true;
-        if (a.dgks) {
+        bool second = !a.single;
+        if (a.dgks || a.single) {
             cluster_sum(cl, S, 1, [&](int) { return sq(); });
             nn = S.tot[0].x;
-            second = !(nn > 0.5 * nb);
+            if (a.dgks && !a.single) second = !(nn > 0.5 * nb);
         }
         if (second) {
             dots(false);
@@ -231,7 +231,7 @@ bool gs_cluster(const GSArgs& a, int nactive, cudaStream_t st) {
     const int Cg = cdiv_up(a.n, (int64_t)GC_THREADS * E);
     // algorithmic bytes: w read and written once; the basis streamed once per
     // pass (two passes with the selective test in its usual outcome, four for CGS2)
-    const double passes = a.cnt == 0 ? 0.0 : (a.dgks ? 2.0 : 4.0);
+    const double passes = a.cnt == 0 ? 0.0 : ((a.dgks || a.single) ? 2.0 : 4.0);
     kprof_begin("gram_schmidt", st);
     switch (E) {
         case 4: launch_gc<4>(a, nactive, Cg, st); break;

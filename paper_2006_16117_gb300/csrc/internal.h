@@ -117,10 +117,11 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
 void spmv_shifted_jobs(const Pencil& P, const JobSpace& js, int nactive, const double* dummy, int x_slot,
                        int y_slot, const double2* d_sigma, cudaStream_t st);
 
-// Arnoldi (CGS2) for all jobs: b = K^{-1} start (start vectors in VS_RHS on
-// entry), beta, V, H, meff.
+// Arnoldi for all jobs: b = K^{-1} start (start vectors in VS_RHS on entry),
+// beta, V, H, meff.  Classical Gram-Schmidt applied twice (CGS2), or once if
+// single_pass (the printed algorithm of Sec. 2).
 bool arnoldi(const Pencil& P, const sim_options& opt, JobSpace& js, const double2* d_sigma,
-             void* const* d_factor_ptrs, cudaStream_t st, InnerStats& stats);
+             void* const* d_factor_ptrs, cudaStream_t st, InnerStats& stats, bool single_pass = false);
 
 void apply_B(const Pencil& P, const double2* x, double2* y, cudaStream_t st);
 

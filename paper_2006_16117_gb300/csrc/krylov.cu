@@ -590,6 +590,22 @@ static void gs_run(GSArgs a, double2* partial, size_t half, int nactive, cudaStr
     size_t sm_upd = ((size_t)a.cnt + 1 + (size_t)(a.cnt + 2) * nw) * sizeof(double2) + 64;
     double2* A = partial;
     double2* Bf = partial + half;
+    if (a.single) {  // one pass: dots, update with the norm, finish
+        a.dgks = 0;
+        a.pout = A;
+        k_gs_dots<<<grid, GS_THREADS, sm_dots, st>>>(a);
+        SIM_LAUNCH_CHECK();
+        a.pin = A;
+        a.pout = Bf;
+        k_gs_update<<<grid, GS_THREADS, sm_upd, st>>>(a, 0, 0);
+        SIM_LAUNCH_CHECK();
+        a.pin = Bf;
+        k_gs_finish<<<grid, GS_THREADS, 0, st>>>(a);
+        SIM_LAUNCH_CHECK();
+        kprof_end("gram_schmidt", st, nactive * (2.0 * a.cnt + 4.0) * a.n * sizeof(double2),
+                  nactive * 16.0 * a.cnt * a.n);
+        return;
+    }
     a.pout = A;
     k_gs_dots<<<grid, GS_THREADS, sm_dots, st>>>(a);
     SIM_LAUNCH_CHECK();
@@ -935,7 +951,7 @@ __global__ void k_store_beta(JobSpace js, int nactive) {
 }
 
 bool arnoldi(const Pencil& P, const sim_options& opt, JobSpace& js, const double2* d_sigma,
-             void* const* d_factor_ptrs, cudaStream_t st, InnerStats& stats) {
+             void* const* d_factor_ptrs, cudaStream_t st, InnerStats& stats, bool single_pass) {
     const int J = js.J, m = js.m;
     std::vector<int> all(J);
     for (int j = 0; j < J; ++j) all[j] = j;
@@ -981,6 +997,7 @@ bool arnoldi(const Pencil& P, const sim_options& opt, JobSpace& js, const double
         a.btol = opt.breakdown_tol;
         a.meff = js.meff;
         a.istat = js.istat;
+        a.single = single_pass ? 1 : 0;
         gs_run(a, js.partial, half, na, st);
         read_state(js, st);
         std::vector<int> next;

@@ -1,5 +1,6 @@
 // Multiplicity step of SIM-M (Sec. 3.4): for every shift σ that resolves
-// clusters, k random vectors f_i give k Krylov spaces K_m^σ(M; b_i); for each
+// clusters, k random vectors f_i give k Krylov spaces K_m^σ(M; b_i) (one
+// classical Gram-Schmidt pass per Arnoldi step unless mult_reorth); for each
 // cluster, P f_i ≈ V_i Σ_j w_j y_ij on a circle around the cluster estimate
 // (radius 2·max(cluster radius, h0), mult_nodes trapezoid nodes), and the
 // multiplicity is the number of singular values of [P f_1 … P f_k] above
@@ -256,7 +257,7 @@ std::vector<int> multiplicities(const MultInput& in, bool& ok) {
             dim3 g1(cdiv_up(n, 256), J);
             k_mult_start<<<g1, 256, 0, st>>>(js, J, k, F);
             SIM_LAUNCH_CHECK();
-            ok = arnoldi(*in.P, o, js, in.d_sigma, in.d_fptrs, st, *in.inner) && ok;
+            ok = arnoldi(*in.P, o, js, in.d_sigma, in.d_fptrs, st, *in.inner, o.mult_reorth == 0) && ok;
             MultArgs a;
             a.js = js;
             a.k = k;

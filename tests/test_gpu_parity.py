@@ -177,6 +177,23 @@ def test_simm_jordan_multiplicity(simlib):
     assert np.array_equal(mult, w.reference_mult)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multiplicity_single_pass_equals_cgs2(simlib, precision):
+    # The multiplicity spaces use one classical Gram-Schmidt pass by default (the
+    # algorithm as printed in Sec. 2); reorthogonalising them (mult_reorth = 1, CGS2
+    # as in the location spaces) gives the same eigenvalues and multiplicities.
+    from workloads import config_jordan_small
+
+    w = config_jordan_small()
+    runs = [simlib.run(w.A, None, w.region, w.f,
+                       simlib.sim_default_options(precision=precision, mult_reorth=r, **w.options))
+            for r in (0, 1)]
+    (eig0, mult0, st0), (eig1, mult1, st1) = runs
+    assert np.array_equal(eig0, eig1)  # location does not depend on the option
+    assert np.array_equal(mult0, mult1)
+    assert np.array_equal(mult0, w.reference_mult)
+
+
 def test_simm_generalized_pencil_vs_dense_qz(simlib):
     import scipy.linalg as sla
 
