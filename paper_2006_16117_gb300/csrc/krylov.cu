@@ -766,6 +766,7 @@ struct Pinned {
     double* sc = nullptr;
     int* act = nullptr;
     int cap = 0;
+    cudaEvent_t act_ev = nullptr;  // the last upload from `act`
     void ensure(int J) {
         if (J <= cap) return;
         if (ist) cudaFreeHost(ist);
@@ -781,8 +782,12 @@ Pinned g_pin;
 
 void upload_active(const JobSpace& js, const std::vector<int>& a, cudaStream_t st) {
     g_pin.ensure(js.J);
+    // the previous upload must have left the pinned buffer before it is refilled
+    if (g_pin.act_ev) SIM_CUDA(cudaEventSynchronize(g_pin.act_ev));
+    else SIM_CUDA(cudaEventCreateWithFlags(&g_pin.act_ev, cudaEventDisableTiming));
     for (size_t i = 0; i < a.size(); ++i) g_pin.act[i] = a[i];
     SIM_CUDA(cudaMemcpyAsync(js.d_active, g_pin.act, sizeof(int) * a.size(), cudaMemcpyHostToDevice, st));
+    SIM_CUDA(cudaEventRecord(g_pin.act_ev, st));
 }
 
 void read_state(const JobSpace& js, cudaStream_t st) {

@@ -194,6 +194,26 @@ def test_multiplicity_single_pass_equals_cgs2(simlib, precision):
     assert np.array_equal(mult0, w.reference_mult)
 
 
+def test_large_n_uses_multi_kernel_gram_schmidt(simlib):
+    # n = 41,209 is beyond the single-launch Gram-Schmidt's range (n <= 40,960),
+    # so the four-kernel version with partial sums in global memory runs here;
+    # the eigenvalues are checked against the closed form.
+    from workloads import cd2d_csr, cd2d_eigenvalues, complex_gaussian
+    from workloads.configs import max_gap_window, window_region
+
+    N = 203
+    A = cd2d_csr(N, (1.0, 0.5))
+    lr = np.sort(cd2d_eigenvalues(N, (1.0, 0.5)).real)
+    start = max_gap_window(lr, 6, lr.size // 2 - 2000, lr.size // 2 + 2000)
+    region = window_region(lr, start, 6)
+    inside = lr[(lr > region[0]) & (lr < region[1])]
+    eig, mult, _ = simlib.run(A, None, region, complex_gaussian(A.n, 3),
+                              simlib.sim_default_options(precision="mixed", h0=1e-6))
+    assert eig.size == inside.size == 6
+    assert np.max(np.abs(np.sort(eig.real) - inside)) <= 1e-6
+    assert np.all(mult == 1)
+
+
 def test_simm_generalized_pencil_vs_dense_qz(simlib):
     import scipy.linalg as sla
 
