@@ -257,7 +257,8 @@ def run_ours(args, world, rank, local):
                "launches": sim.launch_count() - launches0, "eig": eig, "mult": mult, "stats": s.stats()}
         if precision == "mixed":
             rec["clocks"] = clocks.stop()
-            rec["kernels"] = {k: sim.kernel_stats(k) for k in ("block_solve", "factor", "gram_schmidt", "eval_level")}
+            rec["kernels"] = {k: sim.kernel_stats(k)
+                              for k in ("block_solve", "factor", "gram_schmidt", "eval_level", "spmv")}
             sim.kernel_timing(False)
         results[precision] = rec
         s.close()

@@ -181,6 +181,19 @@ sim_status sim_eigenvalues(sim_handle h, double* out, int64_t capacity, int64_t*
  * Errors: SIM_ERR_BAD_STATE (sim_eigenvalues not called), SIM_ERR_CAPACITY. */
 sim_status sim_multiplicity(sim_handle h, int32_t* out, int64_t capacity, int64_t* count);
 
+/* Ritz refinement of the located eigenvalues (Sec. 3.2, Eq. zjHm: the
+ * eigenvalues d_i of a shift's Hessenberg matrix H_m are Ritz values of the
+ * Cayley transform M = (A - σB)^{-1}B, so λ_i = σ + 1/d_i).  For each
+ * eigenvalue of sim_eigenvalues (same order), the λ_i of its resolving shift
+ * nearest the estimate replaces it when within 2·max(cluster radius, h0), the
+ * radius of the multiplicity circle; refined[c] is then 1, else 0 and out[c]
+ * is the estimate.  out: complex128[count] (capacity entries); refined:
+ * int32[count] or NULL.  capacity == 0 only sets *count.  Valid after
+ * sim_eigenvalues until the next sim_set_region; may be called any number
+ * of times.  Errors: SIM_ERR_BAD_STATE, SIM_ERR_CAPACITY,
+ * SIM_ERR_NOT_CONVERGED (a Hessenberg QR iteration hit its sweep limit). */
+sim_status sim_refine(sim_handle h, double* out, int32_t* refined, int64_t capacity, int64_t* count);
+
 /* Copies the counters into *out (size = sizeof(sim_stats_t)). */
 sim_status sim_stats(sim_handle h, sim_stats_t* out, size_t size);
 
@@ -246,7 +259,7 @@ sim_status sim_random_vectors(uint64_t seed, int64_t n, int32_t k, int32_t first
  * Not part of the method: counters used by the benchmark.
  * sim_kernel_timing(1) resets and turns on per-kernel CUDA-event timing of the
  * library's main kernels ("block_solve", "factor", "gram_schmidt",
- * "eval_level"); 0 turns it off.  Process-wide, not thread-safe.
+ * "eval_level", "spmv"); 0 turns it off.  Process-wide, not thread-safe.
  * sim_kernel_stats fills the accumulated device time (ms), algorithmic bytes
  * and flops and launch count of one of them; returns 0 if it never ran.
  * sim_launch_count returns the number of kernel launches the library has made

@@ -18,6 +18,9 @@ Spectral Indicator Method for Eigenvalues of Large Non-Hermitian Matrices"):
   (Sec. 3.1, Eq. DeltaSm) with threshold δ0 (Def. 3.2).
 * Multilevel subdivision (Sec. 3.3) and the SIM-M algorithm (Sec. 3.5).
 * Multiplicity from the rank of [P f_1 … P f_k] (Sec. 3.4).
+* Ritz refinement of the located eigenvalues from the eigenvalues of H_m
+  (Sec. 3.2, Eq. zjHm: H_m = P D P^{-1}; an eigenvalue d of H_m is a Ritz value
+  of M = (A - σB)^{-1}B, and λ = σ + 1/d).
 
 Readings of points the paper leaves open are fixed in ``Options`` and in the
 docstrings below (node angles, weight normalisation, residual normalisation,
@@ -433,6 +436,29 @@ class SimM:
             flagged=flagged[order], radius=rad[order],
         )
         return self.clusters
+
+    # -- Sec. 3.2: Ritz refinement of the located eigenvalues -----------------
+    def refine(self):
+        """For each cluster: the Ritz values d_i = eig(H_m) of its resolving
+        shift's Krylov space (Sec. 3.2, Eq. zjHm), mapped back by λ_i = σ + 1/d_i
+        (the Cayley transform M = (A - σB)^{-1}B has eigenvalues 1/(λ - σ)).
+        The λ_i nearest the cluster estimate replaces it if it lies within
+        2·max(cluster radius, h0) of it (the multiplicity circle's radius);
+        otherwise the estimate stays.  Returns (values, refined flags)."""
+        o = self.o
+        cl = self.clusters
+        est = cl["estimate"]
+        out = est.copy()
+        flag = np.zeros(est.size, dtype=bool)
+        for c in range(est.size):
+            ks = self.spaces[cl["shift"][c]]
+            d = np.linalg.eigvals(ks.H[: ks.m_eff, : ks.m_eff])
+            d = d[d != 0]
+            lam = ks.sigma + 1.0 / d
+            i = int(np.argmin(np.abs(lam - est[c])))
+            if abs(lam[i] - est[c]) <= 2.0 * max(cl["radius"][c], o.h0):
+                out[c], flag[c] = lam[i], True
+        return out, flag
 
     # -- Sec. 3.4: multiplicities ---------------------------------------------
     def multiplicity(self):

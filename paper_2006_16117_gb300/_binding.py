@@ -60,7 +60,7 @@ _lib = None
 
 EXPORTS = [
     "sim_default_options", "sim_create", "sim_set_region", "sim_solve_level", "sim_eigenvalues",
-    "sim_multiplicity", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
+    "sim_multiplicity", "sim_refine", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
     "sim_eval_squares", "sim_apply_shifted", "sim_shifted_solve", "sim_random_vectors",
     "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count", "sim_apply_shifted_noalloc",
 ]
@@ -82,6 +82,7 @@ def lib():
     L.sim_solve_level.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
     L.sim_eigenvalues.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.sim_multiplicity.argtypes = [vp, vp, i64, C.POINTER(i64)]
+    L.sim_refine.argtypes = [vp, vp, vp, i64, C.POINTER(i64)]
     L.sim_stats.argtypes = [vp, C.POINTER(SimStats), C.c_size_t]
     L.sim_last_error.argtypes = [vp]
     L.sim_last_error.restype = C.c_char_p
@@ -234,6 +235,17 @@ class Sim:
         if cnt.value:
             _check(lib().sim_multiplicity(self.h, out.ctypes.data, cnt.value, C.byref(cnt)), self.h)
         return out
+
+    def refine(self):
+        """Ritz-refined eigenvalues (same order as eigenvalues()) and a bool
+        array telling which were refined."""
+        cnt = C.c_int64()
+        _check(lib().sim_refine(self.h, None, None, 0, C.byref(cnt)), self.h)
+        out = np.zeros(cnt.value, dtype=np.complex128)
+        flags = np.zeros(cnt.value, dtype=np.int32)
+        if cnt.value:
+            _check(lib().sim_refine(self.h, out.ctypes.data, flags.ctypes.data, cnt.value, C.byref(cnt)), self.h)
+        return out, flags.astype(bool)
 
     def stats(self) -> dict:
         s = SimStats()

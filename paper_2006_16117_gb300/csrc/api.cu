@@ -16,6 +16,7 @@
 #include "factor_cluster.h"
 #include "levels.h"
 #include "mult.h"
+#include "ritz.h"
 
 using namespace sim;
 
@@ -755,6 +756,37 @@ sim_status sim_multiplicity(sim_handle h, int32_t* out, int64_t capacity, int64_
         if (capacity == 0) return SIM_OK;
         if (capacity < C || !out) return fail(h, SIM_ERR_CAPACITY, "output capacity too small");
         for (int64_t c = 0; c < C; ++c) out[c] = h->mult[c];
+        return SIM_OK;
+    });
+}
+
+sim_status sim_refine(sim_handle h, double* out, int32_t* refined, int64_t capacity, int64_t* count) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (h->state != ST_EIGS) return fail(h, SIM_ERR_BAD_STATE, "call sim_eigenvalues first");
+        const int64_t C = (int64_t)h->eig.size();
+        if (count) *count = C;
+        if (capacity == 0) return SIM_OK;
+        if (capacity < C || !out) return fail(h, SIM_ERR_CAPACITY, "output capacity too small");
+        RitzInput ri;
+        ri.arena = &h->arena;
+        ri.st = h->st;
+        ri.m = h->opt.m;
+        ri.num_slots = h->cap;
+        ri.d_H = h->d_H;
+        ri.d_meff = h->d_meff;
+        ri.d_sigma = h->d_sigma;
+        ri.h0 = h->opt.h0;
+        ri.est = h->eig;
+        ri.shift = h->cl_shift;
+        ri.radius = h->cl_radius;
+        std::vector<double2> vals;
+        std::vector<int> flags;
+        if (!ritz_refine(ri, vals, flags))
+            return fail(h, SIM_ERR_NOT_CONVERGED, "the QR iteration of a Hessenberg matrix did not converge");
+        std::memcpy(out, vals.data(), sizeof(double2) * C);
+        if (refined)
+            for (int64_t c = 0; c < C; ++c) refined[c] = flags[c];
         return SIM_OK;
     });
 }

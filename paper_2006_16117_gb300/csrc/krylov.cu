@@ -353,11 +353,22 @@ __global__ void k_spmv_jobs(Pencil P, JobSpace js, int x_slot, int y_slot, int r
     y[g] = acc;
 }
 
+// y = (A - σB)x (or rhs - (A - σB)x) for the active jobs of the inner solver, timed as "spmv":
+// algorithmic bytes per job 20·nnz + 4(n+1) + 32n (+16n with rhs), 8·nnz flops
+static void launch_spmv(const Pencil& P, const JobSpace& js, int nactive, int x_slot, int y_slot, int rhs_slot,
+                        const double2* d_sigma, cudaStream_t st) {
+    kprof_begin("spmv", st);
+    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), nactive), 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma);
+    SIM_LAUNCH_CHECK();
+    kprof_end("spmv", st, nactive * (20.0 * P.nnz + 4.0 * (P.n + 1) + (rhs_slot >= 0 ? 48.0 : 32.0) * P.n),
+              nactive * 8.0 * P.nnz);
+}
+
 void spmv_shifted_jobs(const Pencil& P, const JobSpace& js, int nactive, const double*, int x_slot, int y_slot,
                        const double2* d_sigma, cudaStream_t st) {
     if (nactive <= 0) return;
-    dim3 grid(cdiv_up(P.n, 256), nactive);
-    k_spmv_jobs<<<grid, 256, 0, st>>>(P, js, x_slot, y_slot, -1, d_sigma);
+    // untimed: also the path of the no-allocation entry point
+    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), nactive), 256, 0, st>>>(P, js, x_slot, y_slot, -1, d_sigma);
     SIM_LAUNCH_CHECK();
 }
 
@@ -860,8 +871,7 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
             if (!js.h_jobshift ||
                 !block_solve_cluster(P, opt.precision, js, act, VS_Q0 + i, vs_Z(k) + i, d_sigma, d_factor_ptrs, st))
                 block_solve(P, opt.precision, js, na, VS_Q0 + i, vs_Z(k) + i, d_sigma, d_factor_ptrs, st);
-            k_spmv_jobs<<<rows_grid(na), 256, 0, st>>>(P, js, vs_Z(k) + i, VS_Q0 + i + 1, -1, d_sigma);
-            SIM_LAUNCH_CHECK();
+            launch_spmv(P, js, na, vs_Z(k) + i, VS_Q0 + i + 1, -1, d_sigma, st);
             GSArgs a{};
             a.basis = js.vec + (size_t)VS_Q0 * js.n;
             a.bstride = js.vstride;
@@ -889,8 +899,7 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
         upload_active(js, in_cycle, st);
         k_gm_update_x<<<rows_grid(ni), 256, 0, st>>>(js);
         SIM_LAUNCH_CHECK();
-        k_spmv_jobs<<<rows_grid(ni), 256, 0, st>>>(P, js, VS_X, VS_R, VS_RHS, d_sigma);
-        SIM_LAUNCH_CHECK();
+        launch_spmv(P, js, ni, VS_X, VS_R, VS_RHS, d_sigma, st);
         {
             GSArgs a{};
             a.w = js.vec + (size_t)VS_R * js.n;

@@ -214,6 +214,36 @@ def test_large_n_uses_multi_kernel_gram_schmidt(simlib):
     assert np.all(mult == 1)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ritz_refinement_matches_oracle_and_closed_form(simlib, precision):
+    # Sec. 3.2: refined eigenvalues σ + 1/d from the Hessenberg QR on the GPU,
+    # against the oracle's refinement (numpy eigvals) and the closed form.
+    from oracle import simm as S
+    from workloads import config_small
+
+    w = config_small()
+    sim = S.SimM(w.A.to_scipy(), None, S.Options(**w.options))
+    sim.set_region(w.region, w.f)
+    sim.solve_levels()
+    sim.merge()
+    ref_o, flag_o = sim.refine()
+    s = simlib.Sim(w.A, None, simlib.sim_default_options(precision=precision, **w.options))
+    try:
+        s.set_region(w.region, w.f)
+        s.solve_all_levels()
+        eig = s.eigenvalues()
+        ref_g, flag_g = s.refine()
+        ref_g2, _ = s.refine()  # repeatable
+    finally:
+        s.close()
+    truth = np.sort_complex(w.reference_eigs)
+    assert eig.size == ref_g.size == ref_o.size == truth.size
+    assert np.array_equal(flag_g, flag_o) and flag_g.all()
+    assert np.array_equal(ref_g, ref_g2)
+    assert np.max(np.abs(ref_g - ref_o)) <= 2e-8
+    assert np.max(np.min(np.abs(ref_g[:, None] - truth[None, :]), axis=1)) <= 1e-8
+
+
 def test_simm_generalized_pencil_vs_dense_qz(simlib):
     import scipy.linalg as sla
 
