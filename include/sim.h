@@ -181,6 +181,17 @@ sim_status sim_eigenvalues(sim_handle h, double* out, int64_t capacity, int64_t*
  * Errors: SIM_ERR_BAD_STATE (sim_eigenvalues not called), SIM_ERR_CAPACITY. */
 sim_status sim_multiplicity(sim_handle h, int32_t* out, int64_t capacity, int64_t* count);
 
+/* The spectral projection P f of the region's vector f onto the eigenspace
+ * of located eigenvalue c (index into sim_eigenvalues' output): the
+ * trapezoid rule of Sec. 2 (Eq. XLXf) on a mult_nodes-node circle of radius
+ * 2·max(cluster radius, h0) around the estimate, through the Krylov space of
+ * f at the cluster's resolving shift (rebuilt, one set of inner solves).  For
+ * a simple eigenvalue this is a right eigenvector (Remark 3.5), unnormalised.
+ * out: complex128[n], caller-allocated.  Valid after sim_eigenvalues until
+ * the next sim_set_region.  Errors: SIM_ERR_BAD_STATE, SIM_ERR_INVALID_ARG
+ * (c out of range, NULL out), SIM_ERR_NOT_CONVERGED. */
+sim_status sim_projection(sim_handle h, int64_t c, double* out);
+
 /* Ritz refinement of the located eigenvalues (Sec. 3.2, Eq. zjHm: the
  * eigenvalues d_i of a shift's Hessenberg matrix H_m are Ritz values of the
  * Cayley transform M = (A - σB)^{-1}B, so λ_i = σ + 1/d_i).  For each

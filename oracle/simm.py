@@ -460,6 +460,24 @@ class SimM:
                 out[c], flag[c] = lam[i], True
         return out, flag
 
+    def projection(self, c):
+        """P f for cluster c: the trapezoid rule (Sec. 2, Eq. XLXf) on the
+        mult_nodes-node circle of radius 2·max(cluster radius, h0) around its
+        estimate, applied to the region's vector f through the Krylov space of
+        the resolving shift (rebuilt with its basis V):
+        P f ≈ V Σ_j ((z_j - c)/N) y_j.  For a simple eigenvalue this is an
+        eigenvector (Remark 3.5)."""
+        o = self.o
+        cl = self.clusters
+        s = cl["shift"][c]
+        ks = cayley_arnoldi(self.A, self.B, self.spaces[s].sigma, self.f, o.m, o.breakdown_tol, keep_basis=True,
+                            lu=self._lu[s])
+        unit = np.exp(2j * np.pi * np.arange(o.mult_nodes) / o.mult_nodes)
+        off = 2.0 * max(cl["radius"][c], o.h0) * unit
+        y, _ = projected_solve(ks, cl["estimate"][c] + off)
+        u = (off / unit.size) @ y
+        return ks.V[:, : ks.m_eff] @ u
+
     # -- Sec. 3.4: multiplicities ---------------------------------------------
     def multiplicity(self):
         """For each shift that resolves clusters: k random vectors f_i, the k

@@ -60,7 +60,7 @@ _lib = None
 
 EXPORTS = [
     "sim_default_options", "sim_create", "sim_set_region", "sim_solve_level", "sim_eigenvalues",
-    "sim_multiplicity", "sim_refine", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
+    "sim_multiplicity", "sim_refine", "sim_projection", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
     "sim_eval_squares", "sim_apply_shifted", "sim_shifted_solve", "sim_random_vectors",
     "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count", "sim_apply_shifted_noalloc",
 ]
@@ -83,6 +83,7 @@ def lib():
     L.sim_eigenvalues.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.sim_multiplicity.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.sim_refine.argtypes = [vp, vp, vp, i64, C.POINTER(i64)]
+    L.sim_projection.argtypes = [vp, i64, vp]
     L.sim_stats.argtypes = [vp, C.POINTER(SimStats), C.c_size_t]
     L.sim_last_error.argtypes = [vp]
     L.sim_last_error.restype = C.c_char_p
@@ -246,6 +247,13 @@ class Sim:
         if cnt.value:
             _check(lib().sim_refine(self.h, out.ctypes.data, flags.ctypes.data, cnt.value, C.byref(cnt)), self.h)
         return out, flags.astype(bool)
+
+    def projection(self, c: int) -> np.ndarray:
+        """P f onto the eigenspace of located eigenvalue c (an eigenvector
+        for a simple eigenvalue), complex128[n]."""
+        out = np.zeros(self.n, dtype=np.complex128)
+        _check(lib().sim_projection(self.h, int(c), out.ctypes.data), self.h)
+        return out
 
     def stats(self) -> dict:
         s = SimStats()

@@ -760,6 +760,29 @@ sim_status sim_multiplicity(sim_handle h, int32_t* out, int64_t capacity, int64_
     });
 }
 
+sim_status sim_projection(sim_handle h, int64_t c, double* out) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (h->state != ST_EIGS) return fail(h, SIM_ERR_BAD_STATE, "call sim_eigenvalues first");
+        if (c < 0 || c >= (int64_t)h->eig.size()) return fail(h, SIM_ERR_INVALID_ARG, "no such eigenvalue");
+        if (!out) return fail(h, SIM_ERR_INVALID_ARG, "NULL output");
+        MultInput mi;
+        mi.P = &h->P;
+        mi.opt = &h->opt;
+        mi.st = h->st;
+        mi.arena = &h->arena;
+        mi.d_sigma = h->d_sigma;
+        mi.d_fptrs = h->d_fptrs;
+        mi.est = h->eig;
+        mi.shift = h->cl_shift;
+        mi.radius = h->cl_radius;
+        mi.inner = &h->inner;
+        if (!projection_vector(mi, h->d_f, (int)c, reinterpret_cast<double2*>(out)))
+            return fail(h, SIM_ERR_NOT_CONVERGED, "an inner shifted solve did not converge");
+        return SIM_OK;
+    });
+}
+
 sim_status sim_refine(sim_handle h, double* out, int32_t* refined, int64_t capacity, int64_t* count) {
     if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
     return guarded(h, [&]() -> sim_status {

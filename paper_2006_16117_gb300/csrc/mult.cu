@@ -315,4 +315,57 @@ std::vector<int> multiplicities(const MultInput& in, bool& ok) {
     return mult;
 }
 
+bool projection_vector(const MultInput& in, const double2* d_f, int c, double2* h_out) {
+    const sim_options& o = *in.opt;
+    DeviceArena& ar = *in.arena;
+    cudaStream_t st = in.st;
+    const int64_t n = in.P->n;
+    const int m = o.m;
+    const int kin = std::max(1, std::min(o.inner_restart, 32));
+    // one Krylov space: f at the cluster's resolving shift, CGS2 as for the location spaces
+    JobSpace js = make_jobspace(ar, st, 1, kin, m, n, "pv_");
+    const int jobshift = in.shift[c];
+    js.h_jobshift = &jobshift;
+    SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, &jobshift, sizeof(int), cudaMemcpyHostToDevice, st));
+    k_mult_start<<<dim3(cdiv_up(n, 256), 1), 256, 0, st>>>(js, 1, 1, d_f);
+    SIM_LAUNCH_CHECK();
+    bool ok = arnoldi(*in.P, o, js, in.d_sigma, in.d_fptrs, st, *in.inner, false);
+    MultArgs a;
+    a.js = js;
+    a.k = 1;
+    a.m = m;
+    a.nodes = o.mult_nodes;
+    a.h0 = o.h0;
+    a.Cp = 1;
+    const int zero = 0, ptr[2] = {0, 1};
+    const double2 est = in.est[c];
+    const double rad = in.radius[c];
+    int* d_job0 = ar.get<int>("pv_job0", 1);
+    double2* d_est = ar.get<double2>("pv_est", 1);
+    double* d_rad = ar.get<double>("pv_rad", 1);
+    int* d_clptr = ar.get<int>("pv_clptr", 2);
+    int* d_cl = ar.get<int>("pv_cl", 1);
+    SIM_CUDA(cudaMemcpyAsync(d_job0, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    SIM_CUDA(cudaMemcpyAsync(d_est, &est, sizeof(double2), cudaMemcpyHostToDevice, st));
+    SIM_CUDA(cudaMemcpyAsync(d_rad, &rad, sizeof(double), cudaMemcpyHostToDevice, st));
+    SIM_CUDA(cudaMemcpyAsync(d_clptr, ptr, sizeof(int) * 2, cudaMemcpyHostToDevice, st));
+    SIM_CUDA(cudaMemcpyAsync(d_cl, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    a.cl_job0 = d_job0;
+    a.cl_est = d_est;
+    a.cl_rad = d_rad;
+    a.u = ar.get<double2>("pv_u", m);
+    a.P = ar.get<double2>("pv_P", n);
+    const size_t sm_proj = ((size_t)m * m + 8 * ((size_t)m * (m + 1) / 2) + 8 * (size_t)m + m) * sizeof(double2);
+    SIM_CUDA(cudaFuncSetAttribute(k_mult_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_proj));
+    k_mult_proj<<<1, 256, sm_proj, st>>>(a, in.d_sigma);
+    SIM_LAUNCH_CHECK();
+    const size_t sm_pf = (size_t)m * PF_ROWS * sizeof(double2);
+    SIM_CUDA(cudaFuncSetAttribute(k_mult_pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_pf));
+    k_mult_pf<<<dim3(cdiv_up(n, PF_ROWS), 1), 256, sm_pf, st>>>(a, d_clptr, d_cl);
+    SIM_LAUNCH_CHECK();
+    SIM_CUDA(cudaMemcpyAsync(h_out, a.P, sizeof(double2) * n, cudaMemcpyDeviceToHost, st));
+    SIM_CUDA(cudaStreamSynchronize(st));
+    return ok;
+}
+
 }  // namespace sim

@@ -23,4 +23,10 @@ struct MultInput {
 
 std::vector<int> multiplicities(const MultInput& in, bool& ok);
 
+// P f of cluster c into h_out (n complex values, host): the trapezoid rule on
+// the mult_nodes-node circle of radius 2·max(radius, h0) around its estimate,
+// through the Krylov space of f at its resolving shift (rebuilt, CGS2).
+// Returns false if an inner solve did not converge.
+bool projection_vector(const MultInput& in, const double2* d_f, int c, double2* h_out);
+
 }  // namespace sim

@@ -244,6 +244,36 @@ def test_ritz_refinement_matches_oracle_and_closed_form(simlib, precision):
     assert np.max(np.min(np.abs(ref_g[:, None] - truth[None, :]), axis=1)) <= 1e-8
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_projection_vector_matches_oracle(simlib, precision):
+    # P f of a located eigenvalue (an eigenvector for a simple one), GPU against
+    # the oracle's, and its eigen-residual with the refined eigenvalue.
+    from oracle import simm as S
+    from workloads import config_small
+
+    w = config_small()
+    A = w.A.to_scipy()
+    sim = S.SimM(A, None, S.Options(**w.options))
+    sim.set_region(w.region, w.f)
+    sim.solve_levels()
+    sim.merge()
+    s = simlib.Sim(w.A, None, simlib.sim_default_options(precision=precision, **w.options))
+    try:
+        s.set_region(w.region, w.f)
+        s.solve_all_levels()
+        s.eigenvalues()
+        ref, _ = s.refine()
+        for c in (0, 17, 49):
+            x = s.projection(c)
+            xo = sim.projection(c)
+            assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+            assert np.linalg.norm(A @ x - ref[c] * x) <= 1e-10 * abs(ref[c]) * np.linalg.norm(x)
+        with pytest.raises(simlib.SimError):
+            s.projection(10**6)
+    finally:
+        s.close()
+
+
 def test_simm_generalized_pencil_vs_dense_qz(simlib):
     import scipy.linalg as sla
 

@@ -269,6 +269,24 @@ def test_ritz_refinement_beats_h0_on_closed_form(small_workload):
                           np.argmin(np.abs(est[:, None] - truth[None, :]), axis=1))
 
 
+def test_projection_is_an_eigenvector(small_workload):
+    # Remark 3.5: for a simple eigenvalue, P f on the cluster's circle is a right
+    # eigenvector.  Checked against dense eig: residual and angle at rounding level.
+    w = small_workload
+    A = w.A.to_scipy()
+    sim = S.SimM(A, None, S.Options(**w.options))
+    sim.set_region(w.region, w.f)
+    sim.solve_levels()
+    sim.merge()
+    ref, _ = sim.refine()
+    lam_d, X = np.linalg.eig(A.toarray())
+    for c in (0, 17, 49):
+        x = sim.projection(c)
+        assert np.linalg.norm(A @ x - ref[c] * x) <= 1e-10 * abs(ref[c]) * np.linalg.norm(x)
+        v = X[:, int(np.argmin(np.abs(lam_d - ref[c])))]
+        assert abs(np.vdot(v, x)) >= (1 - 1e-10) * np.linalg.norm(v) * np.linalg.norm(x)
+
+
 def test_jordan_multiplicity():
     w = config_jordan_small()
     res = S.sim_m(w.A.to_scipy(), None, w.region, w.f, S.Options(**w.options))
