@@ -184,6 +184,11 @@ def cpu_baseline(w_full):
             "seconds": dt, "located": located}
 
 
+def workload_name(w) -> str:
+    return ("convection-diffusion 200x200 (n=40,064) with B=diag(U[1,2]) + 16 Jordan 4x4, "
+            "564 eigenvalues in Re[%.3f, %.3f] x Im[-0.3, 0.7], h0=1e-6, m=50" % w.region[:2])
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -201,7 +206,9 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "eigenvalues/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "sample of the n=40,064 pencil (see cpu_baseline.sample)"},
+            "data": "synthetic",
+            "config": {"workload": workload_name(w), "precision": "FP64 oracle (NumPy/SciPy) on the host cores",
+                       "sample": cb["sample"]},
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": v, "unit": "eigenvalues/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -317,8 +324,7 @@ def run_ours(args, world, rank, local):
         "dtype": "c64+f64",
         "data": "synthetic",
         "config": {
-            "workload": "convection-diffusion 200x200 (n=40,064) with B=diag(U[1,2]) + 16 Jordan 4x4, "
-                        "564 eigenvalues in Re[%.3f, %.3f] x Im[-0.3, 0.7], h0=1e-6, m=50" % w.region[:2],
+            "workload": workload_name(w),
             "precision": "mixed: complex64 block factorisation + FP64 GMRES refinement; FP64 Gram-Schmidt, "
                          "Hessenberg solves and tests",
             "l2": "no flush needed: per-step working set (55 shift factorisations, ~7 GB) exceeds L2",
