@@ -76,6 +76,18 @@ def barrier_max(x: float, world: int) -> float:
     return float(t.item())
 
 
+def allreduce_sum(x: float, world: int) -> float:
+    """Sum of x over the ranks (the units every rank processed)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -260,6 +272,8 @@ def run_ours(args, world, rank, local):
         barrier(world)
         ms = ev0.elapsed_time(ev1)
         ms_max = barrier_max(ms, world)
+        located = int(allreduce_sum(located, world))  # all ranks' units
+        solves = int(allreduce_sum(solves, world))
         rec = {"ms_total": ms_max, "steps": steps, "located": located, "solves": solves,
                "launches": sim.launch_count() - launches0, "eig": eig, "mult": mult, "stats": s.stats()}
         if precision == "mixed":
@@ -305,11 +319,12 @@ def run_ours(args, world, rank, local):
             e2e_times.append(dt)
             e2e_located += int(mult.sum())
     e2e_t = barrier_max(sum(e2e_times), world)
+    e2e_located = int(allreduce_sum(e2e_located, world))
 
     if rank != 0:
         return
     mixed = results["mixed"]
-    value = world * mixed["located"] / (mixed["ms_total"] / 1000.0)
+    value = mixed["located"] / (mixed["ms_total"] / 1000.0)
     line = {
         "metric": METRIC,
         "value": value,
@@ -332,22 +347,23 @@ def run_ours(args, world, rank, local):
             "region_width": args.region_width or None,
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
-        "shifted_solves_per_s": world * mixed["solves"] / (mixed["ms_total"] / 1000.0),
-        "e2e": {"value": world * e2e_located / e2e_t if e2e_t > 0 else None, "unit": "eigenvalues/s",
+        "shifted_solves_per_s": mixed["solves"] / (mixed["ms_total"] / 1000.0),
+        "e2e": {"value": e2e_located / e2e_t if e2e_t > 0 else None, "unit": "eigenvalues/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed.get("clocks"),
     }
     st = mixed["stats"]
-    line["quality"] = {"located_per_step": mixed["located"] // mixed["steps"], "expected": w.expected_count,
+    line["quality"] = {"located_per_step": mixed["located"] // (mixed["steps"] * world),  # per rank
+                       "expected": w.expected_count,
                        "clusters": int(st["clusters"]), "shifts": int(st["num_shifts"]),
                        "max_inner_residual": st["max_inner_residual"],
                        "gmres_iters_per_solve": st["gmres_iterations"] / max(1, st["inner_solves"])}
     if "fp64" in results:
         f = results["fp64"]
-        fv = world * f["located"] / (f["ms_total"] / 1000.0)
+        fv = f["located"] / (f["ms_total"] / 1000.0)
         line["fp64"] = {"value": fv, "unit": "eigenvalues/s", "ms_per_step": f["ms_total"] / f["steps"],
-                        "shifted_solves_per_s": world * f["solves"] / (f["ms_total"] / 1000.0)}
+                        "shifted_solves_per_s": f["solves"] / (f["ms_total"] / 1000.0)}
         line["mixed_over_fp64"] = value / fv
         if f["eig"].size == mixed["eig"].size:
             line["quality"]["max_abs_diff_mixed_vs_fp64"] = float(np.max(np.abs(f["eig"] - mixed["eig"])))
