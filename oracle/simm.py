@@ -61,6 +61,7 @@ class Options:
     mult_seed: int = 0x5EED
     residual_scale: str = "solution"  # "solution": ρ relative to ||y|| = ||x_m||; "beta": relative to β = ||b||
     max_squares: int = 4_000_000    # a level with more squares than this is an error
+    mult_reorth: int = 0            # multiplicity spaces: 0 one Gram-Schmidt pass (as printed), 1 CGS2
 
 
 # ---------------------------------------------------------------------------
@@ -81,13 +82,14 @@ def shifted_factor(A, B, sigma):
     return spla.splu(K)
 
 
-def cayley_arnoldi(A, B, sigma, f, m, breakdown_tol=1e-14, keep_basis=False, lu=None):
+def cayley_arnoldi(A, B, sigma, f, m, breakdown_tol=1e-14, keep_basis=False, lu=None, passes=2):
     """Arnoldi for M = (A - σB)^{-1}B started from b = (A - σB)^{-1}f.
 
     Sec. 2: v_1 = b/||b||, then for j = 1..m: w = M v_j, h_ij = (w, v_i),
     w -= Σ h_ij v_i, h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}; stop if
-    h_{j+1,j} = 0.  The projection is applied twice (CGS2) and the two sets of
-    coefficients summed.  "Zero" is h_{j+1,j} <= breakdown_tol * ||H_{1:j+1,1:j}||_F.
+    h_{j+1,j} = 0.  The projection is applied `passes` times (2: CGS2, the
+    default; 1: the single pass as printed) and the coefficients summed.
+    "Zero" is h_{j+1,j} <= breakdown_tol * ||H_{1:j+1,1:j}||_F.
     """
     n = A.shape[0]
     if lu is None:
@@ -103,11 +105,12 @@ def cayley_arnoldi(A, B, sigma, f, m, breakdown_tol=1e-14, keep_basis=False, lu=
     for j in range(m):
         w = lu.solve(B @ V[:, j])
         Vj = V[:, : j + 1]
-        h1 = Vj.conj().T @ w
-        w = w - Vj @ h1
-        h2 = Vj.conj().T @ w
-        w = w - Vj @ h2
-        H[: j + 1, j] = h1 + h2
+        h = np.zeros(j + 1, dtype=np.complex128)
+        for _ in range(passes):
+            hp = Vj.conj().T @ w
+            w = w - Vj @ hp
+            h = h + hp
+        H[: j + 1, j] = h
         hn = float(np.linalg.norm(w))
         if hn <= breakdown_tol * float(np.linalg.norm(H[: j + 1, : j + 1])):
             m_eff = j + 1
@@ -514,7 +517,8 @@ class SimM:
         k = F.shape[1]
         Pf = np.zeros((members.size, self.n, k), dtype=np.complex128)
         for i in range(k):
-            ks = cayley_arnoldi(self.A, self.B, sigma, F[:, i], o.m, o.breakdown_tol, keep_basis=True, lu=lu)
+            ks = cayley_arnoldi(self.A, self.B, sigma, F[:, i], o.m, o.breakdown_tol, keep_basis=True, lu=lu,
+                                passes=2 if o.mult_reorth else 1)
             self.n_inner_solves += 1 + ks.m_eff
             for q, c in enumerate(members):
                 rc = 2.0 * max(cl["radius"][c], o.h0)
