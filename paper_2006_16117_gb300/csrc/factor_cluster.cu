@@ -33,7 +33,9 @@ __device__ __forceinline__ double2 sval(const Pencil& P, int64_t e, double2 sg) 
     return make_double2(a.x - (sg.x * b.x - sg.y * b.y), a.y - (sg.x * b.y + sg.y * b.x));
 }
 
-template <class C> __device__ __forceinline__ double m1(C a) { return fabs((double)a.x) + fabs((double)a.y); }
+// pivot magnitude |re| + |im| in the factor's own precision (float for complex64:
+// FP64 on this GPU is slow and the pivot search is on every pivot's critical path)
+template <class C> __device__ __forceinline__ auto m1(C a) -> decltype(a.x) { return fabs(a.x) + fabs(a.y); }
 
 }  // namespace
 
@@ -60,9 +62,10 @@ __global__ void __launch_bounds__(256, 1) k_factor_cl(Pencil P, const int* shift
     int* piv_row = reinterpret_cast<int*>(prow + T);  // [T] pivot row of column p (all CTAs)
     int* step_of = piv_row + T;                  // [T] column at which row r was the pivot
     int* used = step_of + T;                     // [Tc]
-    double* cand_v = reinterpret_cast<double*>(used + Tc + (Tc & 1) + 2);  // [8]
+    using Mt = decltype(zc<C>().x);
+    Mt* cand_v = reinterpret_cast<Mt*>(used + Tc + (Tc & 1) + 2);        // [8]
     int* cand_i = reinterpret_cast<int*>(cand_v + 8);                    // [8]
-    double* red_v = reinterpret_cast<double*>(cand_i + 8);               // [8 warps]
+    Mt* red_v = reinterpret_cast<Mt*>(cand_i + 8);                       // [8 warps]
     int* red_i = reinterpret_cast<int*>(red_v + 8);                      // [8 warps]
 
     for (int64_t e = tid + (int64_t)q * blockDim.x; e < P.nnzL; e += (int64_t)blockDim.x * Cf)
@@ -108,18 +111,18 @@ __global__ void __launch_bounds__(256, 1) k_factor_cl(Pencil P, const int* shift
         __syncthreads();
         // 2. Gauss–Jordan with implicit partial pivoting
         for (int p = 0; p < T; ++p) {
-            double bv = -1.0;
+            Mt bv = Mt(-1);
             int bi = T;
             for (int i = tid; i < my; i += blockDim.x) {
                 if (used[i]) continue;
-                const double v = m1(S[(size_t)i * T + p]);
+                const Mt v = m1(S[(size_t)i * T + p]);
                 if (v > bv || (v == bv && r0 + i < bi)) {
                     bv = v;
                     bi = r0 + i;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const Mt ov = __shfl_xor_sync(0xffffffffu, bv, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ov > bv || (ov == bv && oi < bi)) {
                     bv = ov;
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(256, 1) k_factor_cl(Pencil P, const int* shift
             }
             __syncthreads();
             if (tid < Cf) {
-                double v = red_v[0];
+                Mt v = red_v[0];
                 int ii = red_i[0];
                 for (int w = 1; w < nw; ++w)
                     if (red_v[w] > v || (red_v[w] == v && red_i[w] < ii)) {
@@ -143,14 +146,14 @@ __global__ void __launch_bounds__(256, 1) k_factor_cl(Pencil P, const int* shift
                 *cl.map_shared_rank(cand_i + q, tid) = ii;
             }
             cl.sync();
-            double v = cand_v[0];
+            Mt v = cand_v[0];
             int rs = cand_i[0];
             for (int w = 1; w < Cf; ++w)
                 if (cand_v[w] > v || (cand_v[w] == v && cand_i[w] < rs)) {
                     v = cand_v[w];
                     rs = cand_i[w];
                 }
-            if (!(v > 0.0) && tid == 0 && q == 0) atomicExch(err, 1);  // singular Schur complement
+            if (!(v > Mt(0)) && tid == 0 && q == 0) atomicExch(err, 1);  // singular Schur complement
             if (tid == 0) {
                 piv_row[p] = rs;
                 step_of[rs] = p;
