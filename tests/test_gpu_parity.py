@@ -292,6 +292,47 @@ def test_simm_generalized_pencil_vs_dense_qz(simlib):
     assert np.all(mult == 1)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_refinement_and_projection_on_generalized_pencil(simlib, precision):
+    # B ≠ I: GPU refined eigenvalues against dense QZ and the oracle, and P f
+    # against A x = λ B x and the oracle's P f.
+    import scipy.linalg as sla
+
+    from oracle import simm as S
+    from workloads import cd2d_csr, diag_csr
+
+    N = 15
+    A0 = cd2d_csr(N, (1.0, 0.5))
+    bd = np.random.default_rng(11).uniform(1.0, 2.0, A0.n)
+    Ad, Bd = A0.to_dense(), np.diag(bd)
+    lam = sla.eigvals(Ad, Bd)
+    lr = np.sort(lam.real)
+    lo, hi = 0.5 * (lr[99] + lr[100]), 0.5 * (lr[119] + lr[120])
+    inside = lam[(lam.real > lo) & (lam.real < hi)]
+    region = (lo, hi, -0.3, 0.7)
+    f = np.random.default_rng(12).standard_normal(A0.n) + 0j
+    sim = S.SimM(A0.to_scipy(), diag_csr(bd).to_scipy(), S.Options(h0=1e-6))
+    sim.set_region(region, f)
+    sim.solve_levels()
+    sim.merge()
+    ref_o, flag_o = sim.refine()
+    s = simlib.Sim(A0, diag_csr(bd), simlib.sim_default_options(precision=precision, h0=1e-6))
+    try:
+        s.set_region(region, f)
+        s.solve_all_levels()
+        s.eigenvalues()
+        ref, flag = s.refine()
+        assert flag.all() and np.array_equal(flag, flag_o)
+        assert np.max(np.min(np.abs(ref[:, None] - inside[None, :]), axis=1)) <= 1e-8
+        assert np.max(np.abs(ref - ref_o)) <= 2e-8
+        for c in (0, 9, 19):
+            x = s.projection(c)
+            assert np.linalg.norm(x - sim.projection(c)) <= 1e-8 * np.linalg.norm(x)
+            assert np.linalg.norm(Ad @ x - ref[c] * (Bd @ x)) <= 1e-8 * abs(ref[c]) * np.linalg.norm(Bd @ x)
+    finally:
+        s.close()
+
+
 def test_simm_laplacian_degenerate_multiplicity(simlib):
     from oracle import simm as S
     from workloads import cd2d_csr

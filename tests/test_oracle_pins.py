@@ -247,6 +247,34 @@ def test_generalized_pencil_vs_dense_qz():
     assert count_below(N, (1.0, 0.5), bd, hi) - count_below(N, (1.0, 0.5), bd, lo) == 20
 
 
+def _generalized_case():
+    N = 15
+    A0 = cd2d_csr(N, (1.0, 0.5))
+    bd = np.random.default_rng(11).uniform(1.0, 2.0, A0.n)
+    A, B = A0.to_scipy(), diag_csr(bd).to_scipy()
+    lam = sla.eigvals(A.toarray(), B.toarray())
+    lr = np.sort(lam.real)
+    lo, hi = 0.5 * (lr[99] + lr[100]), 0.5 * (lr[119] + lr[120])
+    f = np.random.default_rng(12).standard_normal(A0.n) + 0j
+    return A0, bd, A, B, lam[(lam.real > lo) & (lam.real < hi)], (lo, hi, -0.3, 0.7), f
+
+
+def test_refinement_and_projection_on_generalized_pencil():
+    # B ≠ I: the refined values σ + 1/d against dense QZ, and P f against A x = λ B x.
+    _, _, A, B, inside, region, f = _generalized_case()
+    sim = S.SimM(A, B, S.Options(h0=1e-6))
+    sim.set_region(region, f)
+    sim.solve_levels()
+    sim.merge()
+    ref, flag = sim.refine()
+    assert flag.all() and ref.size == inside.size == 20
+    assert _match(ref, inside, 1.0) <= 1e-8
+    Ad, Bd = A.toarray(), B.toarray()
+    for c in (0, 9, 19):
+        x = sim.projection(c)
+        assert np.linalg.norm(Ad @ x - ref[c] * (Bd @ x)) <= 1e-8 * abs(ref[c]) * np.linalg.norm(Bd @ x)
+
+
 def test_ritz_refinement_beats_h0_on_closed_form(small_workload):
     # Sec. 3.2: λ = σ + 1/d over the eigenvalues d of H_m.  Against the closed
     # form, every refined eigenvalue of the 50-eigenvalue case is far inside h0
