@@ -16,6 +16,11 @@
  *   sim_eigenvalues   — step 6-7 (merge, output)
  *   sim_multiplicity  — Sec. 3.4
  *
+ * and, optional after sim_eigenvalues:
+ *
+ *   sim_refine        — Ritz refinement of the eigenvalues      Sec. 3.2
+ *   sim_projection    — P f of one eigenvalue (an eigenvector)  Remark 3.5
+ *
  * Conventions shared by every call:
  *  - Complex numbers are complex128 stored as interleaved (re, im) doubles.
  *  - Every call returns a sim_status and never throws; a handle's last error
