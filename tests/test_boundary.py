@@ -62,6 +62,9 @@ def test_null_arguments_are_rejected_without_a_gpu(built):
     assert b"CSR" in lib.sim_last_error(None) or len(lib.sim_last_error(None)) > 0
     assert lib.sim_solve_level(None, None, None) == 1
     assert lib.sim_eigenvalues(None, None, 0, None) == 1
+    assert lib.sim_multiplicity(None, None, 0, None) == 1
+    assert lib.sim_refine(None, None, None, 0, None) == 1
+    assert lib.sim_projection(None, 0, None) == 1
     lib.sim_destroy(None)
 
 
