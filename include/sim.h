@@ -126,6 +126,8 @@ typedef struct {
     int64_t clusters;
     double max_inner_residual;           /* worst relative residual of an inner solve */
     double t_factor_ms, t_krylov_ms, t_levels_ms, t_merge_ms, t_mult_ms;
+    int64_t loose_inner_solves;          /* inner solves that stagnated above inner_tol and were
+                                            accepted within 100·inner_tol */
 } sim_stats_t;
 
 /* Fills *opt with the defaults listed above.  opt must not be NULL. */
@@ -257,13 +259,20 @@ sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const d
  * fragment that pool, or a latency-critical loop that cannot afford the device
  * synchronisation cudaMalloc/cudaFree may cause.  The paper has no counterpart:
  * this is a deployment variant of the sparse apply.  It stages x and y in one
- * file-scope device array (n <= 262,144 complex128 per vector, about 8 MiB,
- * held by every GPU that loads the library until exit) and calls no
- * cudaMalloc, cudaFree or other allocating routine.  The array's device
- * address is looked up on the first call made on each device (make that first
- * call before any stream capture).  Calls share the array: each call fully
- * overwrites what it reads, and calls that overlap on the GPU race.
- * Errors: SIM_ERR_LIMIT when n exceeds 262,144; SIM_ERR_INVALID_ARG; SIM_ERR_CUDA. */
+ * file-scope device array (n <= 262,144 complex128 per vector, about 8 MiB)
+ * and calls no cudaMalloc, cudaFree or other allocating routine.  The CUDA
+ * runtime reserves the array on a device when it loads the library's module
+ * there: with the default lazy module loading, during the first call made on
+ * that device (with CUDA_MODULE_LOADING=EAGER, at context creation).  Make
+ * that first call, or set CUDA_MODULE_LOADING=EAGER, before another allocator
+ * reserves the GPU; the device keeps the array until the process exits.  The
+ * first call on each device also looks up the array's device address (make it
+ * before any stream capture).  Calls share the array: each call fully
+ * overwrites what it reads, and calls that overlap on the GPU race.  The call
+ * is synchronous: it returns once y is written.
+ * Errors: SIM_ERR_LIMIT when n exceeds 262,144; SIM_ERR_INVALID_ARG;
+ * SIM_ERR_OOM when loading the array fails for lack of device memory;
+ * SIM_ERR_CUDA. */
 sim_status sim_apply_shifted_noalloc(sim_handle h, double sig_re, double sig_im, const double* x, double* y);
 
 /* Philox4x64-10 complex Gaussian vectors: out[v*n + e] for v < k is element e

@@ -50,6 +50,7 @@ class SimStats(C.Structure):
         ("unresolvable_final", C.c_int64), ("final_squares", C.c_int64), ("clusters", C.c_int64),
         ("max_inner_residual", C.c_double), ("t_factor_ms", C.c_double), ("t_krylov_ms", C.c_double),
         ("t_levels_ms", C.c_double), ("t_merge_ms", C.c_double), ("t_mult_ms", C.c_double),
+        ("loose_inner_solves", C.c_int64),
     ]
 
     def as_dict(self):

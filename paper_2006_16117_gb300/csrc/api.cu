@@ -262,6 +262,7 @@ void sync_stats(sim_ctx* h) {
     h->stats.gmres_iterations = h->inner.iters;
     h->stats.max_gmres_iterations = h->inner.max_iters;
     h->stats.max_inner_residual = h->inner.worst;
+    h->stats.loose_inner_solves = h->inner.loose;
 }
 
 }  // namespace

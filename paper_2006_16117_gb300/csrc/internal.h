@@ -88,7 +88,7 @@ __host__ __device__ inline int vs_count(int k) { return VS_Q0 + 2 * k + 1; }
 
 // scal / istat fields
 enum { SC_RNORM0 = 0, SC_RES = 1, SC_GAMMA = 2, SC_WORST = 3, SC_N = 8 };
-enum { IS_STEPS = 0, IS_ITERS = 1, IS_DONE = 2, IS_CYCLE_DONE = 3, IS_BROKEN = 4, IS_N = 8 };
+enum { IS_STEPS = 0, IS_ITERS = 1, IS_DONE = 2, IS_CYCLE_DONE = 3, IS_BROKEN = 4, IS_STALL = 5, IS_LOOSE = 6, IS_N = 8 };
 
 constexpr int GS_CHUNK = 1024;   // rows per CTA in the Gram–Schmidt kernels
 constexpr int GS_THREADS = 256;
@@ -99,14 +99,11 @@ constexpr int GS_THREADS = 256;
 void factor_shifts(const Pencil& P, int precision, const int* d_shift_list, int count,
                    const double2* d_sigma, void* const* d_factor_ptrs, cudaStream_t st);
 
-// z_job = P^{-1} q_job for active jobs (vector slots given).
-void block_solve(const Pencil& P, int precision, const JobSpace& js, int nactive, int in_slot,
-                 int out_slot, const double2* d_sigma, void* const* d_factor_ptrs, cudaStream_t st);
-
 // Batched FGMRES for (A - σB) x = rhs on the jobs listed on the host; x in
 // VS_X.  Returns false if some job hit the iteration cap.
 struct InnerStats {
     int64_t solves = 0, iters = 0;
+    int64_t loose = 0;  // solves accepted above inner_tol (within 100x) after stagnating
     int max_iters = 0;
     double worst = 0.0;
 };

@@ -9,15 +9,21 @@
 // allocates on first use; this variant stages them in one file-scope device
 // array instead and calls no cudaMalloc, cudaFree or other allocating routine.
 //
-// The array holds at most SIM_NOALLOC_MAX_N complex128 entries per vector.
-// Every GPU that loads the library keeps the array (about 8 MiB) until the
-// process exits.  In host code the array's name is only a stand-in for it, so
-// the device address is obtained with cudaGetSymbolAddress once per device, on
-// the first call made while that device is current; make that first call
-// before any stream capture.  All calls share the array and it keeps the last
-// call's contents: each call overwrites both staging vectors completely before
-// reading them, and calls that overlap on the GPU (different streams or
-// handles at once) race on it.
+// The array holds at most SIM_NOALLOC_MAX_N complex128 entries per vector
+// (about 8 MiB in all).  The CUDA runtime reserves it on a device when it
+// loads this file's module there: at context creation with
+// CUDA_MODULE_LOADING=EAGER, otherwise (lazy loading, the default) on the
+// first call made on that device.  A caller whose pool will later reserve the
+// GPU should make that first call, or set CUDA_MODULE_LOADING=EAGER, before
+// the pool does; an out-of-memory result of that load is reported as
+// SIM_ERR_OOM.  The device keeps the array until the process exits.  In host
+// code the array's name is only a stand-in for it, so the device address is
+// obtained with cudaGetSymbolAddress once per device, on the first call made
+// while that device is current; make that first call before any stream
+// capture.  All calls share the array and it keeps the last call's contents:
+// each call overwrites both staging vectors completely before reading them,
+// and calls that overlap on the GPU (different streams or handles at once)
+// race on it.  The call is synchronous: it returns once y is written.
 #include <cstring>
 #include <string>
 
@@ -70,23 +76,26 @@ extern "C" sim_status sim_apply_shifted_noalloc(sim_handle h, double sig_re, dou
     using namespace sim;
     NoallocView v;
     if (!h || !noalloc_view(h, &v)) return SIM_ERR_INVALID_ARG;
-    if (!x || !y) {
-        noalloc_fail(h, "sim_apply_shifted_noalloc: NULL vector");
-        return SIM_ERR_INVALID_ARG;
-    }
-    const int64_t n = v.P->n;
-    if (n > SIM_NOALLOC_MAX_N) {
-        noalloc_fail(h, "sim_apply_shifted_noalloc: n = " + std::to_string(n) + " exceeds the static scratch limit of " +
-                            std::to_string(SIM_NOALLOC_MAX_N) + "; use sim_apply_shifted");
-        return SIM_ERR_LIMIT;
-    }
-    double2* base = nullptr;
-    cudaError_t e = scratch_address(&base);
-    if (e != cudaSuccess) {
-        noalloc_fail(h, std::string("sim_apply_shifted_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        return SIM_ERR_CUDA;
-    }
     try {
+        noalloc_fail(h, "");  // clear the previous call's message
+        if (!x || !y) {
+            noalloc_fail(h, "sim_apply_shifted_noalloc: NULL vector");
+            return SIM_ERR_INVALID_ARG;
+        }
+        const int64_t n = v.P->n;
+        if (n > SIM_NOALLOC_MAX_N) {
+            noalloc_fail(h, "sim_apply_shifted_noalloc: n = " + std::to_string(n) +
+                                " exceeds the static scratch limit of " + std::to_string(SIM_NOALLOC_MAX_N) +
+                                "; use sim_apply_shifted");
+            return SIM_ERR_LIMIT;
+        }
+        double2* base = nullptr;
+        cudaError_t e = scratch_address(&base);
+        if (e != cudaSuccess) {
+            noalloc_fail(h, std::string("sim_apply_shifted_noalloc: cudaGetSymbolAddress (loads the static scratch "
+                                        "array on first use): ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA;
+        }
         const double2 sg = make_double2(sig_re, sig_im);
         const int idx[2] = {0, v.scratch_slot};  // active job 0, its shift id
         SIM_CUDA(cudaMemcpyAsync(v.d_sigma + v.scratch_slot, &sg, sizeof(double2), cudaMemcpyHostToDevice, v.st));
@@ -104,6 +113,10 @@ extern "C" sim_status sim_apply_shifted_noalloc(sim_handle h, double sig_re, dou
         SIM_CUDA(cudaStreamSynchronize(v.st));
     } catch (const CudaError& err) {
         noalloc_fail(h, "sim_apply_shifted_noalloc: " + err.what);
+        return err.code == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA;
+    } catch (const std::bad_alloc&) {
+        return SIM_ERR_OOM;  // host memory for the message itself ran out
+    } catch (...) {
         return SIM_ERR_CUDA;
     }
     return SIM_OK;

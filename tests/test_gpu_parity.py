@@ -76,6 +76,34 @@ def test_shifted_solve_matches_sparse_lu(simlib, precision):
     assert iters >= 1
 
 
+def _cd2d_rect(nx, ny, beta=(1.0, 0.5)):
+    """-Δu + β·∇u on an nx × ny interior grid of the unit square, x fastest:
+    band half-width nx."""
+    def d1(N, b):
+        h = 1.0 / (N + 1)
+        return sp.diags([(-1 / h**2 - b / (2 * h)) * np.ones(N - 1), 2 / h**2 * np.ones(N),
+                         (-1 / h**2 + b / (2 * h)) * np.ones(N - 1)], [-1, 0, 1])
+    A = sp.kron(sp.identity(ny), d1(nx, beta[0])) + sp.kron(d1(ny, beta[1]), sp.identity(nx))
+    return sp.csr_matrix(A, dtype=np.complex128)
+
+
+@pytest.mark.parametrize("precision,nx", [("fp64", 340), ("mixed", 470)])
+def test_shifted_solve_single_cta_factorisation(simlib, precision, nx):
+    """Blocks of side nx = 340 (complex128) or 470 (complex64) do not fit a
+    cluster's shared memory: the single-CTA factorisation runs instead."""
+    A = _cd2d_rect(nx, 3)
+    A.sort_indices()
+    s = simlib.Sim(_csr_arrays(A), None, simlib.sim_default_options(precision=precision))
+    assert s.stats()["block_size"] == nx
+    r = np.random.default_rng(11).standard_normal(A.shape[0]) + 0.25j
+    sigma = 1.2e5 + 0.3j
+    x, iters, rel = s.shifted_solve(sigma, torch.from_numpy(r).cuda())
+    ref = spla.splu((A - sigma * sp.identity(A.shape[0])).tocsc()).solve(r)
+    assert rel <= 1e-12
+    assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
+    s.close()
+
+
 def _perturbed_spread(S, ks, centers, sides, name, trials=3, rel=4e-16):
     """How far rounding-size perturbations of H move the oracle's outputs:
     the conditioning bound a correct GPU result must stay within."""
@@ -162,6 +190,7 @@ def test_simm_small_convection_diffusion(simlib, small_oracle, precision):
     assert np.array_equal(mult, ref.multiplicities)
     assert st["unresolvable_final"] == 0
     assert st["max_inner_residual"] <= 100 * opt.mult_inner_tol  # worst accepted inner solve
+    assert st["loose_inner_solves"] == 0
 
 
 def test_simm_jordan_multiplicity(simlib):
@@ -380,13 +409,22 @@ def test_invalid_csr_is_rejected(simlib):
 # ---------------------------------------------------------------------------
 # the benchmark configuration at full size: n = 40,064, B diagonal, Jordan blocks
 # ---------------------------------------------------------------------------
-@pytest.fixture(scope="module")
-def pencil_run(simlib):
+@pytest.fixture(scope="module", params=["mixed", "fp64"])
+def pencil_run(simlib, request):
     from workloads import config_pencil
 
     w = config_pencil()
-    opt = simlib.sim_default_options(precision="mixed", **w.options)
-    eig, mult, st = simlib.run(w.A, w.B, w.region, w.f, opt)
+    opt = simlib.sim_default_options(precision=request.param, **w.options)
+    s = simlib.Sim(w.A, w.B, opt)
+    try:
+        s.set_region(w.region, w.f)
+        marked = s.solve_all_levels()
+        eig = s.eigenvalues()
+        mult = s.multiplicity()
+        st = s.stats()
+    finally:
+        s.close()
+    st["marked_per_level"] = marked
     return w, eig, mult, st
 
 
@@ -416,3 +454,4 @@ def test_pencil_sampled_eigenvalues_by_inertia(pencil_run):
     for x in rng.choice(real, 6, replace=False):
         # exactly one eigenvalue of the pencil within 2e-6 of each sampled estimate
         assert count_below(200, (1.0, 0.5), bd, x + 2e-6) - count_below(200, (1.0, 0.5), bd, x - 2e-6) == 1
+

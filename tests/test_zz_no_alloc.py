@@ -57,6 +57,45 @@ def test_noalloc_apply_matches_allocating_apply_on_consecutive_calls(simlib):
     s.close()
 
 
+def test_noalloc_apply_leaves_free_device_memory_unchanged(simlib):
+    """After the first call on the device (which loads the static array), a
+    call must not change the device's free memory: it allocates nothing."""
+    from workloads import cd2d_csr
+
+    A = cd2d_csr(30, (1.0, 0.5))
+    s = simlib.Sim(A, None)
+    lib = simlib.lib()
+    rng = np.random.default_rng(7)
+    x = torch.from_numpy(rng.standard_normal(A.n) + 1j * rng.standard_normal(A.n)).cuda()
+    y = torch.empty_like(x)
+    args = (s.h, 100.0, 0.5, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()))
+    assert lib.sim_apply_shifted_noalloc(*args) == 0, lib.sim_last_error(s.h)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert lib.sim_apply_shifted_noalloc(*args) == 0, lib.sim_last_error(s.h)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    s.close()
+
+
+def test_noalloc_apply_at_its_static_limit_matches_allocating_apply(simlib):
+    from workloads import tridiag_toeplitz_csr
+
+    n = 262144  # the largest n the static array holds
+    T = tridiag_toeplitz_csr(n, -1.0 + 0.25j, 2.0, -1.0)
+    s = simlib.Sim(T, None)
+    lib = simlib.lib()
+    rng = np.random.default_rng(8)
+    x = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n)).cuda()
+    st_ref, y_ref = _apply(simlib, s, lib.sim_apply_shifted, 1.5 - 0.5j, x)
+    st, y = _apply(simlib, s, lib.sim_apply_shifted_noalloc, 1.5 - 0.5j, x)
+    assert st_ref == 0 and st == 0, lib.sim_last_error(s.h)
+    ref = y_ref.cpu().numpy()
+    assert np.max(np.abs(y.cpu().numpy() - ref)) <= 1e-13 * np.max(np.abs(ref))
+    s.close()
+
+
 def test_noalloc_apply_rejects_sizes_beyond_its_static_limit(simlib):
     from workloads import tridiag_toeplitz_csr
 
