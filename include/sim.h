@@ -144,6 +144,25 @@ void sim_default_options(sim_options* opt);
 sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt,
                       void* stream, sim_handle* out);
 
+/* Optional, between sim_create and sim_set_region: replaces the inner
+ * solver's preconditioner for (A - σB).  The paper leaves the solver of the
+ * shifted systems open (Sec. 2, Eqs. AzBxf, IMxb); by default this library
+ * factors A - σB per shift as a block-tridiagonal matrix, whose memory grows
+ * as n times the band width.  Pencils whose principal part is separable —
+ *   A ≈ A_s = Σ_d I ⊗ … ⊗ T_d ⊗ … ⊗ I   (axis 0 fastest, n = Π dims[d]),
+ *   T_d = tridiag(sub_d, diag_d, sup_d) Toeplitz of order dims[d],  B = b·I,
+ * e.g. finite-difference convection–diffusion–reaction on a box — can use the
+ * fast-diagonalisation inverse (Lynch, Rice, Thomas 1964) of A_s - σB as the
+ * preconditioner instead: O(n) memory per Krylov job, O(Σ dims[d]²) per
+ * pencil, nothing factored per shift.  The flexible GMRES around it corrects
+ * for A - A_s (reaction terms), so the results do not depend on the choice;
+ * only the iteration count does.  axes: complex128 (sub, diag, sup) per axis,
+ * i.e. 6·ndim doubles.  The handle's previous region (if any) is discarded.
+ * Errors: SIM_ERR_INVALID_ARG (ndim outside 1..3, a length outside 1..8192,
+ * Π dims != n, B not a multiple of I, a zero off-diagonal, non-finite
+ * entries), SIM_ERR_OOM, SIM_ERR_CUDA. */
+sim_status sim_set_separable(sim_handle h, int32_t ndim, const int64_t* dims, const double* axes);
+
 /* Sets the search region R = [re_lo, re_hi] × [im_lo, im_hi] and the random
  * vector f (complex128[n]; f_on_device selects host or device memory; f ==
  * NULL draws f from Philox4x64-10 with key (seed, 0x53494D4D), vector index 0).

@@ -64,6 +64,7 @@ EXPORTS = [
     "sim_multiplicity", "sim_refine", "sim_projection", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
     "sim_eval_squares", "sim_apply_shifted", "sim_shifted_solve", "sim_random_vectors",
     "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count", "sim_apply_shifted_noalloc",
+    "sim_set_separable",
 ]
 
 
@@ -80,6 +81,7 @@ def lib():
     L.sim_default_options.restype = None
     L.sim_create.argtypes = [C.POINTER(SimCsr), C.POINTER(SimCsr), C.POINTER(SimOptions), vp, C.POINTER(vp)]
     L.sim_set_region.argtypes = [vp, dbl, dbl, dbl, dbl, vp, i32, u64]
+    L.sim_set_separable.argtypes = [vp, i32, vp, vp]
     L.sim_solve_level.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
     L.sim_eigenvalues.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.sim_multiplicity.argtypes = [vp, vp, i64, C.POINTER(i64)]
@@ -194,6 +196,15 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+    def set_separable(self, dims, axes):
+        """Fast-diagonalisation preconditioner for a separable principal part:
+        dims = axis lengths (axis 0 fastest), axes = [(sub, diag, sup), ...]
+        complex per axis (include/sim.h, sim_set_separable)."""
+        d = np.ascontiguousarray(dims, dtype=np.int64)
+        a = np.ascontiguousarray(np.asarray(axes, dtype=np.complex128).reshape(-1))
+        assert a.size == 3 * d.size
+        _check(lib().sim_set_separable(self.h, int(d.size), d.ctypes.data, a.ctypes.data), self.h)
 
     def set_region(self, region, f=None, seed=0):
         re_lo, re_hi, im_lo, im_hi = (float(x) for x in region)

@@ -16,7 +16,9 @@
 #include "factor_cluster.h"
 #include "levels.h"
 #include "mult.h"
+#include "adjoint.h"
 #include "ritz.h"
+#include "separable.h"
 
 using namespace sim;
 
@@ -73,10 +75,42 @@ struct sim_ctx {
     std::vector<int> mult;
     sim_stats_t stats{};
     InnerStats inner;
+    // B = b_value·I (identity, or a diagonal with one value): the separable
+    // preconditioner needs it
+    bool b_scalar = false;
+    double2 b_value = {1.0, 0.0};
+    std::unique_ptr<SepCtx> sep;
+    // the pencil's union pattern on the host (for the adjoint pencil and value
+    // updates), and A's / B's own entries: row, column, position in the union
+    std::vector<int32_t> u_rp, u_ci;
+    std::vector<double2> u_Ka, u_Kb, u_bd;
+    bool has_B = false;
+    int64_t nnzA = 0, nnzB = 0;
+    int32_t *d_arow = nullptr, *d_acol = nullptr, *d_amap = nullptr;
+    int32_t *d_brow = nullptr, *d_bcol = nullptr, *d_bmap = nullptr;
+    // adjoint pencil (A^H, B^H), built on first use by the gradient calls
+    Pencil Padj;
+    bool adj_built = false;
+    std::unique_ptr<SepCtx> sep_adj;
+    // node solves of the gradient calls: per direction (0 forward, 1 adjoint)
+    // a shift table of the quadrature nodes and, for the band preconditioner,
+    // a factorisation per node
+    double2* d_nsig[2] = {nullptr, nullptr};
+    void** d_nfptrs[2] = {nullptr, nullptr};
+    std::vector<void*> nfactors[2];
+    // forward state of sim_projection_norm for sim_projection_norm_grad
+    bool pn_valid = false, pn_kept = false;
+    std::vector<double2> pn_z, pn_w;
+    double2* d_pn_X = nullptr;  // [N][n] node solutions (when kept)
+    double2* d_pn_x = nullptr;  // [n] P f
+    double2* d_pn_f = nullptr;  // [n] f
 
     ~sim_ctx() {
         for (void* p : factors)
             if (p) cudaFree(p);
+        for (auto& v : nfactors)
+            for (void* p : v)
+                if (p) cudaFree(p);
     }
 };
 
@@ -102,6 +136,12 @@ template <class F> sim_status guarded(sim_ctx* h, F&& f) {
         if (w.rfind("LIMIT:", 0) == 0) return fail(h, SIM_ERR_LIMIT, w.substr(6));
         return fail(h, SIM_ERR_CUDA, w);
     }
+}
+
+void* up_buf(sim_ctx* h, const std::string& name, const void* src, size_t bytes) {
+    void* d = h->arena.get<unsigned char>(name, (int64_t)bytes);
+    if (bytes) SIM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, h->st));
+    return d;
 }
 
 struct HostCsr {
@@ -150,6 +190,86 @@ bool fetch_csr(const sim_csr* A, HostCsr& out, std::string& why) {
         }
     }
     return true;
+}
+
+// Band layout and device arrays of a pencil given on its union pattern (rows
+// rp/ci, A's values Ka and B's values Kb on it, B's kind and diagonal).
+void upload_pencil(DeviceArena& ar, cudaStream_t st, Pencil& P, const std::vector<int32_t>& rp,
+                   const std::vector<int32_t>& ci, const std::vector<double2>& Ka, const std::vector<double2>& Kb,
+                   int b_kind, const std::vector<double2>& bd, const std::string& tag) {
+    const int64_t n = (int64_t)rp.size() - 1;
+    int64_t kl = 0, ku = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            kl = std::max<int64_t>(kl, i - ci[e]);
+            ku = std::max<int64_t>(ku, ci[e] - i);
+        }
+    P.n = n;
+    P.nnz = (int64_t)ci.size();
+    P.T = (int)std::max<int64_t>(2, std::max(kl, ku));
+    P.T += P.T & 1;  // even: block rows stay 16-byte aligned in complex64
+    P.nb = (int)((n + P.T - 1) / P.T);
+    P.b_kind = b_kind;
+    // couplings to the next block row, column-compressed per block
+    const int T = P.T, nb = P.nb;
+    std::vector<int32_t> up_ptr((size_t)nb * (T + 1), 0), up_row, up_idx;
+    {
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> cols(T);
+        for (int k = 0; k + 1 < nb; ++k) {
+            for (auto& c : cols) c.clear();
+            for (int i = 0; i < T; ++i) {
+                int64_t g = (int64_t)k * T + i;
+                if (g >= n) break;
+                for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
+                    int64_t j = ci[e];
+                    if (j >= (int64_t)(k + 1) * T) cols[j - (int64_t)(k + 1) * T].push_back({i, (int32_t)e});
+                }
+            }
+            size_t base = (size_t)k * (T + 1);
+            up_ptr[base] = (int32_t)up_row.size();
+            for (int c = 0; c < T; ++c) {
+                for (auto& pr : cols[c]) {
+                    up_row.push_back(pr.first);
+                    up_idx.push_back(pr.second);
+                }
+                up_ptr[base + c + 1] = (int32_t)up_row.size();
+            }
+        }
+    }
+    // couplings to the previous block row
+    std::vector<int32_t> Lptr(n + 1, 0), Lcol, Lidx;
+    for (int64_t g = 0; g < n; ++g) {
+        const int64_t k = g / T;
+        for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
+            const int64_t j = ci[e];
+            if (k > 0 && j < k * T && j >= (k - 1) * T) {
+                Lcol.push_back((int32_t)(j - (k - 1) * T));
+                Lidx.push_back((int32_t)e);
+            }
+        }
+        Lptr[g + 1] = (int32_t)Lcol.size();
+    }
+    auto up = [&](const char* name, const void* src, size_t bytes) -> void* {
+        void* d = ar.get<unsigned char>(tag + name, (int64_t)bytes);
+        if (bytes) SIM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st));
+        return d;
+    };
+    P.rp = (const int32_t*)up("rp", rp.data(), sizeof(int32_t) * rp.size());
+    P.ci = (const int32_t*)up("ci", ci.data(), sizeof(int32_t) * ci.size());
+    P.Ka = (const double2*)up("Ka", Ka.data(), sizeof(double2) * Ka.size());
+    P.Kb = (const double2*)up("Kb", Kb.data(), sizeof(double2) * Kb.size());
+    P.Bdiag = (const double2*)up("Bd", bd.data(), sizeof(double2) * bd.size());
+    P.up_ptr = (const int32_t*)up("upp", up_ptr.data(), sizeof(int32_t) * up_ptr.size());
+    P.up_row = (const int32_t*)up("upr", up_row.data(), sizeof(int32_t) * up_row.size());
+    P.up_idx = (const int32_t*)up("upi", up_idx.data(), sizeof(int32_t) * up_idx.size());
+    P.Lptr = (const int32_t*)up("Lptr", Lptr.data(), sizeof(int32_t) * Lptr.size());
+    P.Lcol = (const int32_t*)up("Lcol", Lcol.data(), sizeof(int32_t) * Lcol.size());
+    P.Lidx = (const int32_t*)up("Lidx", Lidx.data(), sizeof(int32_t) * Lidx.size());
+    P.nnzL = (int64_t)Lcol.size();
+    std::vector<int32_t> L0col(n);
+    for (int64_t g = 0; g < n; ++g) L0col[g] = Lptr[g + 1] > Lptr[g] ? Lcol[Lptr[g]] : -1;
+    P.L0col = (const int32_t*)up("L0col", L0col.data(), sizeof(int32_t) * L0col.size());
+    SIM_CUDA(cudaStreamSynchronize(st));
 }
 
 void ensure_shift_capacity(sim_ctx* h) {
@@ -205,34 +325,43 @@ __global__ void k_store_space(JobSpace js, int J, const int* job_shift, double2*
 // A - σB, b = (A - σB)^{-1} f, m Arnoldi steps).  Returns false on non-convergence.
 bool build_shifts(sim_ctx* h, const std::vector<double2>& sig) {
     if (sig.empty()) return true;
-    const int J = (int)sig.size();
-    if (h->S + J > h->opt.max_shifts) throw std::runtime_error("LIMIT:too many shifts (max_shifts)");
-    std::vector<int> ids(J);
-    for (int j = 0; j < J; ++j) {
-        ids[j] = h->S + j;
-        h->h_sigma[ids[j]] = sig[j];
+    const int Jall = (int)sig.size();
+    if (h->S + Jall > h->opt.max_shifts) throw std::runtime_error("LIMIT:too many shifts (max_shifts)");
+    // Krylov jobs per batch: as many as fit the device memory budget of job spaces
+    const int Jmax = max_jobs_for_memory(h->P.n, h->opt.m, std::max(1, std::min(h->opt.inner_restart, 32)));
+    bool ok = true;
+    for (int b0 = 0; b0 < Jall; b0 += Jmax) {
+        const int J = std::min(Jmax, Jall - b0);
+        std::vector<int> ids(J);
+        for (int j = 0; j < J; ++j) {
+            ids[j] = h->S + j;
+            h->h_sigma[ids[j]] = sig[b0 + j];
+        }
+        SIM_CUDA(cudaMemcpyAsync(h->d_sigma + h->S, sig.data() + b0, sizeof(double2) * J, cudaMemcpyHostToDevice,
+                                 h->st));
+        if (!h->P.sep) {
+            for (int s : ids) factor_storage(h, s);
+            int* d_list = h->arena.get<int>("shift_list", J);
+            SIM_CUDA(cudaMemcpyAsync(d_list, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
+            Timer tf(h->st);
+            if (!factor_shifts_cluster(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st))
+                factor_shifts(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st);
+            h->stats.t_factor_ms += tf.ms();
+        }
+        Timer tk(h->st);
+        JobSpace js = make_jobspace(h, J, "loc_");
+        js.h_jobshift = ids.data();
+        SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
+        dim3 grid(cdiv_up(h->P.n, 256), J);
+        k_copy_start<<<grid, 256, 0, h->st>>>(js, J, h->d_f);
+        SIM_LAUNCH_CHECK();
+        ok = arnoldi(h->P, h->opt, js, h->d_sigma, h->d_fptrs, h->st, h->inner) && ok;
+        k_store_space<<<J, 256, 0, h->st>>>(js, J, js.d_jobshift, h->d_H, h->d_beta, h->d_meff, h->opt.m);
+        SIM_LAUNCH_CHECK();
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        h->S += J;
+        h->stats.t_krylov_ms += tk.ms();
     }
-    SIM_CUDA(cudaMemcpyAsync(h->d_sigma + h->S, sig.data(), sizeof(double2) * J, cudaMemcpyHostToDevice, h->st));
-    for (int s : ids) factor_storage(h, s);
-    int* d_list = h->arena.get<int>("shift_list", J);
-    SIM_CUDA(cudaMemcpyAsync(d_list, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
-    Timer tf(h->st);
-    if (!factor_shifts_cluster(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st))
-        factor_shifts(h->P, h->opt.precision, d_list, J, h->d_sigma, h->d_fptrs, h->st);
-    h->stats.t_factor_ms += tf.ms();
-    Timer tk(h->st);
-    JobSpace js = make_jobspace(h, J, "loc_");
-    js.h_jobshift = ids.data();
-    SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, ids.data(), sizeof(int) * J, cudaMemcpyHostToDevice, h->st));
-    dim3 grid(cdiv_up(h->P.n, 256), J);
-    k_copy_start<<<grid, 256, 0, h->st>>>(js, J, h->d_f);
-    SIM_LAUNCH_CHECK();
-    bool ok = arnoldi(h->P, h->opt, js, h->d_sigma, h->d_fptrs, h->st, h->inner);
-    k_store_space<<<J, 256, 0, h->st>>>(js, J, js.d_jobshift, h->d_H, h->d_beta, h->d_meff, h->opt.m);
-    SIM_LAUNCH_CHECK();
-    SIM_CUDA(cudaStreamSynchronize(h->st));
-    h->S += J;
-    h->stats.t_krylov_ms += tk.ms();
     return ok;
 }
 
@@ -263,6 +392,127 @@ void sync_stats(sim_ctx* h) {
     h->stats.max_gmres_iterations = h->inner.max_iters;
     h->stats.max_inner_residual = h->inner.worst;
     h->stats.loose_inner_solves = h->inner.loose;
+}
+
+
+// ---------------------------------------------------------------------------
+// node solves for the gradient calls
+// ---------------------------------------------------------------------------
+EntryList entries_A(sim_ctx* h) { return EntryList{h->d_arow, h->d_acol, h->d_amap, h->nnzA}; }
+EntryList entries_B(sim_ctx* h) { return EntryList{h->d_brow, h->d_bcol, h->d_bmap, h->nnzB}; }
+
+// The adjoint pencil (A^H, B^H) on the transposed union pattern, and its
+// separable part (the conjugate transposes of the axis factors) if any.
+void ensure_adjoint(sim_ctx* h) {
+    if (h->adj_built) return;
+    const int64_t n = h->P.n;
+    const std::vector<int32_t>& rp = h->u_rp;
+    const std::vector<int32_t>& ci = h->u_ci;
+    std::vector<int32_t> rpt(n + 1, 0), cit(ci.size());
+    std::vector<double2> Kat(ci.size()), Kbt(ci.size());
+    for (int32_t c : ci) ++rpt[c + 1];
+    for (int64_t i = 0; i < n; ++i) rpt[i + 1] += rpt[i];
+    std::vector<int32_t> pos(rpt.begin(), rpt.end() - 1);
+    for (int64_t i = 0; i < n; ++i)  // rows in increasing order: each transposed row's columns stay sorted
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t d = pos[ci[e]]++;
+            cit[d] = (int32_t)i;
+            Kat[d] = make_double2(h->u_Ka[e].x, -h->u_Ka[e].y);
+            Kbt[d] = make_double2(h->u_Kb[e].x, -h->u_Kb[e].y);
+        }
+    std::vector<double2> bdt(n);
+    for (int64_t i = 0; i < n; ++i) bdt[i] = make_double2(h->u_bd[i].x, -h->u_bd[i].y);
+    upload_pencil(h->arena, h->st, h->Padj, rpt, cit, Kat, Kbt, h->P.b_kind, bdt, "Padj_");
+    if (h->sep) {
+        auto sa = std::make_unique<SepCtx>();
+        sa->S = h->sep->S;
+        for (int d = 0; d < sa->S.ndim; ++d) {
+            const double2 sub = h->sep->S.axis[d][0], dg = h->sep->S.axis[d][1], sup = h->sep->S.axis[d][2];
+            sa->S.axis[d][0] = make_double2(sup.x, -sup.y);
+            sa->S.axis[d][1] = make_double2(dg.x, -dg.y);
+            sa->S.axis[d][2] = make_double2(sub.x, -sub.y);
+        }
+        sa->S.b = make_double2(h->sep->S.b.x, -h->sep->S.b.y);
+        sa->ar = &h->arena;
+        separable_setup(sa->S, h->arena, h->st, "sepadj_");
+        h->sep_adj = std::move(sa);
+        h->Padj.sep = h->sep_adj.get();
+    }
+    h->adj_built = true;
+}
+
+__global__ void k_nodes_in(JobSpace js, int J, const double2* rhs, int64_t stride) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (g >= js.n || j >= J) return;
+    js.vec[(size_t)j * js.vstride + (size_t)VS_RHS * js.n + g] = rhs[(size_t)j * stride + g];
+}
+
+__global__ void k_nodes_out(JobSpace js, int J, double2* out) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (g >= js.n || j >= J) return;
+    out[(size_t)j * js.n + g] = js.vec[(size_t)j * js.vstride + (size_t)VS_X * js.n + g];
+}
+
+// out_j = (A - z_j B)^{-1} rhs_j (dir 0) or (A - z_j B)^{-H} rhs_j (dir 1) for
+// j < N, by the inner solver (FGMRES with the handle's preconditioner at each
+// node); rhs_j = rhs + j * rhs_stride, out: [N][n].  False on non-convergence.
+bool solve_nodes(sim_ctx* h, int dir, const std::vector<double2>& z, const double2* rhs, int64_t rhs_stride,
+                 double2* out) {
+    const int N = (int)z.size();
+    if (dir) ensure_adjoint(h);
+    const Pencil& P = dir ? h->Padj : h->P;
+    std::vector<double2> zs(N);
+    for (int j = 0; j < N; ++j) zs[j] = dir ? make_double2(z[j].x, -z[j].y) : z[j];
+    const std::string tag = dir ? "nadj_" : "nfwd_";
+    h->d_nsig[dir] = h->arena.get<double2>(tag + "sig", 64);
+    h->d_nfptrs[dir] = h->arena.get<void*>(tag + "fptrs", 64);
+    SIM_CUDA(cudaMemcpyAsync(h->d_nsig[dir], zs.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, h->st));
+    std::vector<int> ids(N);
+    for (int j = 0; j < N; ++j) ids[j] = j;
+    if (!P.sep) {
+        auto& fac = h->nfactors[dir];
+        if ((int)fac.size() < N) fac.resize(N, nullptr);
+        for (int j = 0; j < N; ++j)
+            if (!fac[j]) {
+                cudaError_t e = cudaMalloc(&fac[j], h->factor_bytes);
+                if (e != cudaSuccess) throw CudaError{e, "cudaMalloc of a node factorisation"};
+            }
+        SIM_CUDA(cudaMemcpyAsync(h->d_nfptrs[dir], fac.data(), sizeof(void*) * N, cudaMemcpyHostToDevice, h->st));
+        int* d_list = h->arena.get<int>(tag + "list", N);
+        SIM_CUDA(cudaMemcpyAsync(d_list, ids.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->st));
+        if (!factor_shifts_cluster(P, h->opt.precision, d_list, N, h->d_nsig[dir], h->d_nfptrs[dir], h->st))
+            factor_shifts(P, h->opt.precision, d_list, N, h->d_nsig[dir], h->d_nfptrs[dir], h->st);
+    }
+    JobSpace js = sim::make_jobspace(h->arena, h->st, N, std::max(1, std::min(h->opt.inner_restart, 32)), 1, P.n,
+                                     tag);
+    js.h_jobshift = ids.data();
+    SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, ids.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->st));
+    const dim3 grid(cdiv_up(P.n, 256), N);
+    k_nodes_in<<<grid, 256, 0, h->st>>>(js, N, rhs, rhs_stride);
+    SIM_LAUNCH_CHECK();
+    bool ok = inner_solve(P, h->opt, js, ids, h->d_nsig[dir], h->d_nfptrs[dir], h->st, h->inner);
+    k_nodes_out<<<grid, 256, 0, h->st>>>(js, N, out);
+    SIM_LAUNCH_CHECK();
+    SIM_CUDA(cudaStreamSynchronize(h->st));
+    return ok;
+}
+
+// z_j = c + r e^{2πij/N} and the normalised trapezoid weights (z_j - c)/N
+void circle_nodes(double2 c, double r, int N, std::vector<double2>& z, std::vector<double2>& w) {
+    z.resize(N);
+    w.resize(N);
+    for (int j = 0; j < N; ++j) {
+        const double a = 2.0 * M_PI * j / N;
+        const double ox = r * std::cos(a), oy = r * std::sin(a);
+        z[j] = make_double2(c.x + ox, c.y + oy);
+        w[j] = make_double2(ox / N, oy / N);
+    }
+}
+
+void copy_out(void* dst, const void* src, size_t bytes, int on_device, cudaStream_t st) {
+    SIM_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
 }
 
 }  // namespace
@@ -351,7 +601,7 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
         ci.reserve(a.ci.size() + (hasB ? b.ci.size() : n));
         bool bdiag = true;
         std::vector<double2> bd(n, make_double2(hasB ? 0.0 : 1.0, 0.0));
-        int64_t kl = 0, ku = 0;
+        std::vector<int32_t> amap(a.ci.size()), bmap(hasB ? b.ci.size() : 0);
         for (int64_t i = 0; i < n; ++i) {
             int64_t ea = a.rp[i], eb = hasB ? b.rp[i] : 0;
             const int64_t fa = a.rp[i + 1], fb = hasB ? b.rp[i + 1] : 0;
@@ -361,9 +611,15 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
                 int64_t jb = hasB ? (eb < fb ? b.ci[eb] : INT64_MAX) : (diag_done ? INT64_MAX : i);
                 int64_t j = std::min(ja, jb);
                 double2 va = make_double2(0, 0), vb = make_double2(0, 0);
-                if (ja == j) va = a.v[ea++];
+                if (ja == j) {
+                    amap[ea] = (int32_t)ci.size();
+                    va = a.v[ea++];
+                }
                 if (jb == j) {
-                    if (hasB) vb = b.v[eb++];
+                    if (hasB) {
+                        bmap[eb] = (int32_t)ci.size();
+                        vb = b.v[eb++];
+                    }
                     else {
                         vb = make_double2(1.0, 0.0);
                         diag_done = true;
@@ -376,77 +632,37 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
                 ci.push_back((int32_t)j);
                 Ka.push_back(va);
                 Kb.push_back(vb);
-                kl = std::max<int64_t>(kl, i - j);
-                ku = std::max<int64_t>(ku, j - i);
             }
             rp[i + 1] = (int32_t)ci.size();
         }
         Pencil& P = h->P;
-        P.n = n;
-        P.nnz = (int64_t)ci.size();
-        P.T = (int)std::max<int64_t>(2, std::max(kl, ku));
-        P.T += P.T & 1;  // even: block rows stay 16-byte aligned in complex64
-        P.nb = (int)((n + P.T - 1) / P.T);
-        P.b_kind = hasB ? (bdiag ? 1 : 2) : 0;
-        // couplings to the next block row, column-compressed per block
+        upload_pencil(h->arena, h->st, P, rp, ci, Ka, Kb, hasB ? (bdiag ? 1 : 2) : 0, bd, "P_");
         const int T = P.T, nb = P.nb;
-        std::vector<int32_t> up_ptr((size_t)nb * (T + 1), 0), up_row, up_idx;
+        h->u_rp = std::move(rp);
+        h->u_ci = std::move(ci);
+        h->u_Ka = std::move(Ka);
+        h->u_Kb = std::move(Kb);
+        h->u_bd = bd;
+        h->has_B = hasB;
         {
-            std::vector<std::vector<std::pair<int32_t, int32_t>>> cols(T);
-            for (int k = 0; k + 1 < nb; ++k) {
-                for (auto& c : cols) c.clear();
-                for (int i = 0; i < T; ++i) {
-                    int64_t g = (int64_t)k * T + i;
-                    if (g >= n) break;
-                    for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
-                        int64_t j = ci[e];
-                        if (j >= (int64_t)(k + 1) * T) cols[j - (int64_t)(k + 1) * T].push_back({i, (int32_t)e});
-                    }
-                }
-                size_t base = (size_t)k * (T + 1);
-                up_ptr[base] = (int32_t)up_row.size();
-                for (int c = 0; c < T; ++c) {
-                    for (auto& pr : cols[c]) {
-                        up_row.push_back(pr.first);
-                        up_idx.push_back(pr.second);
-                    }
-                    up_ptr[base + c + 1] = (int32_t)up_row.size();
-                }
+            // rows, columns and union positions of A's (and B's) own entries
+            std::vector<int32_t> row(a.ci.size());
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t e = a.rp[i]; e < a.rp[i + 1]; ++e) row[e] = (int32_t)i;
+            h->nnzA = (int64_t)a.ci.size();
+            h->d_arow = (int32_t*)up_buf(h.get(), "A_row", row.data(), sizeof(int32_t) * row.size());
+            h->d_acol = (int32_t*)up_buf(h.get(), "A_col", a.ci.data(), sizeof(int32_t) * a.ci.size());
+            h->d_amap = (int32_t*)up_buf(h.get(), "A_map", amap.data(), sizeof(int32_t) * amap.size());
+            if (hasB) {
+                std::vector<int32_t> brow(b.ci.size());
+                for (int64_t i = 0; i < n; ++i)
+                    for (int64_t e = b.rp[i]; e < b.rp[i + 1]; ++e) brow[e] = (int32_t)i;
+                h->nnzB = (int64_t)b.ci.size();
+                h->d_brow = (int32_t*)up_buf(h.get(), "B_row", brow.data(), sizeof(int32_t) * brow.size());
+                h->d_bcol = (int32_t*)up_buf(h.get(), "B_col", b.ci.data(), sizeof(int32_t) * b.ci.size());
+                h->d_bmap = (int32_t*)up_buf(h.get(), "B_map", bmap.data(), sizeof(int32_t) * bmap.size());
             }
         }
-        // couplings to the previous block row
-        std::vector<int32_t> Lptr(n + 1, 0), Lcol, Lidx;
-        for (int64_t g = 0; g < n; ++g) {
-            const int64_t k = g / T;
-            for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
-                const int64_t j = ci[e];
-                if (k > 0 && j < k * T && j >= (k - 1) * T) {
-                    Lcol.push_back((int32_t)(j - (k - 1) * T));
-                    Lidx.push_back((int32_t)e);
-                }
-            }
-            Lptr[g + 1] = (int32_t)Lcol.size();
-        }
-        auto up = [&](const char* name, const void* src, size_t bytes) -> void* {
-            void* d = h->arena.get<unsigned char>(name, (int64_t)bytes);
-            if (bytes) SIM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, h->st));
-            return d;
-        };
-        P.rp = (const int32_t*)up("P_rp", rp.data(), sizeof(int32_t) * rp.size());
-        P.ci = (const int32_t*)up("P_ci", ci.data(), sizeof(int32_t) * ci.size());
-        P.Ka = (const double2*)up("P_Ka", Ka.data(), sizeof(double2) * Ka.size());
-        P.Kb = (const double2*)up("P_Kb", Kb.data(), sizeof(double2) * Kb.size());
-        P.Bdiag = (const double2*)up("P_Bd", bd.data(), sizeof(double2) * bd.size());
-        P.up_ptr = (const int32_t*)up("P_upp", up_ptr.data(), sizeof(int32_t) * up_ptr.size());
-        P.up_row = (const int32_t*)up("P_upr", up_row.data(), sizeof(int32_t) * up_row.size());
-        P.up_idx = (const int32_t*)up("P_upi", up_idx.data(), sizeof(int32_t) * up_idx.size());
-        P.Lptr = (const int32_t*)up("P_Lptr", Lptr.data(), sizeof(int32_t) * Lptr.size());
-        P.Lcol = (const int32_t*)up("P_Lcol", Lcol.data(), sizeof(int32_t) * Lcol.size());
-        P.Lidx = (const int32_t*)up("P_Lidx", Lidx.data(), sizeof(int32_t) * Lidx.size());
-        P.nnzL = (int64_t)Lcol.size();
-        std::vector<int32_t> L0col(n);
-        for (int64_t g = 0; g < n; ++g) L0col[g] = Lptr[g + 1] > Lptr[g] ? Lcol[Lptr[g]] : -1;
-        P.L0col = (const int32_t*)up("P_L0col", L0col.data(), sizeof(int32_t) * L0col.size());
         SIM_CUDA(cudaStreamSynchronize(h->st));
         const size_t cs = o.precision == SIM_FP64 ? sizeof(double2) : sizeof(float2);
         h->factor_bytes = ((size_t)2 * nb * (size_t)T * T + (size_t)P.nnzL + (size_t)n + 16) * cs;
@@ -457,6 +673,15 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
         h->stats.nnz_B = hasB ? (int64_t)b.ci.size() : n;
         h->stats.block_size = T;
         h->stats.num_blocks = nb;
+        if (P.b_kind == 0) {
+            h->b_scalar = true;
+            h->b_value = make_double2(1.0, 0.0);
+        } else if (P.b_kind == 1) {
+            h->b_scalar = true;
+            h->b_value = bd[0];
+            for (int64_t i = 1; i < n && h->b_scalar; ++i)
+                h->b_scalar = bd[i].x == bd[0].x && bd[i].y == bd[0].y;
+        }
         return SIM_OK;
     });
     if (s != SIM_OK) return s;
@@ -896,11 +1121,13 @@ sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const d
         const double2 sg = make_double2(sig_re, sig_im);
         h->h_sigma[sc] = sg;
         SIM_CUDA(cudaMemcpyAsync(h->d_sigma + sc, &sg, sizeof(double2), cudaMemcpyHostToDevice, h->st));
-        factor_storage(h, sc);
-        int* d_list = h->arena.get<int>("cmp_list", 1);
-        SIM_CUDA(cudaMemcpyAsync(d_list, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
-        if (!factor_shifts_cluster(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st))
-            factor_shifts(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st);
+        if (!h->P.sep) {
+            factor_storage(h, sc);
+            int* d_list = h->arena.get<int>("cmp_list", 1);
+            SIM_CUDA(cudaMemcpyAsync(d_list, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
+            if (!factor_shifts_cluster(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st))
+                factor_shifts(h->P, h->opt.precision, d_list, 1, h->d_sigma, h->d_fptrs, h->st);
+        }
         JobSpace js = make_jobspace(h, 1, "cmp_");
         js.h_jobshift = &sc;
         SIM_CUDA(cudaMemcpyAsync(js.d_jobshift, &sc, sizeof(int), cudaMemcpyHostToDevice, h->st));
@@ -913,6 +1140,179 @@ sim_status sim_shifted_solve(sim_handle h, double sig_re, double sig_im, const d
         if (iters) *iters = (int32_t)is.iters;
         if (relres) *relres = is.worst;
         if (!ok) return fail(h, SIM_ERR_NOT_CONVERGED, "shifted solve did not converge");
+        return SIM_OK;
+    });
+}
+
+sim_status sim_set_separable(sim_handle h, int32_t ndim, const int64_t* dims, const double* axes) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (ndim < 1 || ndim > 3 || !dims || !axes) return fail(h, SIM_ERR_INVALID_ARG, "ndim must be 1..3");
+        int64_t prod = 1;
+        for (int d = 0; d < ndim; ++d) {
+            if (dims[d] < 1 || dims[d] > 8192) return fail(h, SIM_ERR_INVALID_ARG, "axis length out of range (1..8192)");
+            prod *= dims[d];
+        }
+        if (prod != h->P.n) return fail(h, SIM_ERR_INVALID_ARG, "the axis lengths' product differs from n");
+        if (!h->b_scalar) return fail(h, SIM_ERR_INVALID_ARG, "B is not a multiple of the identity");
+        auto sep = std::make_unique<SepCtx>();
+        sep->S.ndim = ndim;
+        sep->S.b = h->b_value;
+        for (int d = 0; d < ndim; ++d) {
+            sep->S.dims[d] = dims[d];
+            for (int e = 0; e < 3; ++e) {
+                const double re = axes[6 * d + 2 * e], im = axes[6 * d + 2 * e + 1];
+                if (!std::isfinite(re) || !std::isfinite(im)) return fail(h, SIM_ERR_INVALID_ARG, "non-finite axis entry");
+                sep->S.axis[d][e] = make_double2(re, im);
+            }
+            const double2 sub = sep->S.axis[d][0], sup = sep->S.axis[d][2];
+            if (dims[d] > 1 && ((sub.x == 0 && sub.y == 0) || (sup.x == 0 && sup.y == 0)))
+                return fail(h, SIM_ERR_INVALID_ARG, "an axis with a zero off-diagonal is not diagonalisable");
+        }
+        sep->ar = &h->arena;
+        separable_setup(sep->S, h->arena, h->st);
+        // the factorisations of an earlier region are no longer used
+        for (int s = 0; s < h->cap; ++s) {
+            if (h->factors[s]) {
+                cudaFree(h->factors[s]);
+                h->factors[s] = nullptr;
+            }
+        }
+        h->sep = std::move(sep);
+        h->P.sep = h->sep.get();
+        h->S = 0;
+        h->state = ST_CREATED;
+        return SIM_OK;
+    });
+}
+
+sim_status sim_projection_norm(sim_handle h, double c_re, double c_im, double radius, int32_t nodes, const double* f,
+                               int32_t f_on_device, int32_t keep, double* phi) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (!f || !phi || !(radius > 0) || !std::isfinite(radius) || nodes < 4 || nodes > 64 || !std::isfinite(c_re) ||
+            !std::isfinite(c_im))
+            return fail(h, SIM_ERR_INVALID_ARG, "bad argument (radius > 0, 4 <= nodes <= 64, f and phi non-NULL)");
+        const int64_t n = h->P.n;
+        h->pn_valid = false;
+        circle_nodes(make_double2(c_re, c_im), radius, nodes, h->pn_z, h->pn_w);
+        h->d_pn_f = h->arena.get<double2>("pn_f", n);
+        h->d_pn_x = h->arena.get<double2>("pn_x", n);
+        SIM_CUDA(cudaMemcpyAsync(h->d_pn_f, f, sizeof(double2) * n,
+                                 f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+        double2* X = h->arena.get<double2>("pn_X", (int64_t)nodes * n);
+        if (!solve_nodes(h, 0, h->pn_z, h->d_pn_f, 0, X)) return fail(h, SIM_ERR_NOT_CONVERGED, "node solve did not converge");
+        double2* d_w = h->arena.get<double2>("pn_w", 64);
+        SIM_CUDA(cudaMemcpyAsync(d_w, h->pn_w.data(), sizeof(double2) * nodes, cudaMemcpyHostToDevice, h->st));
+        combine_nodes(X, nodes, n, d_w, false, h->d_pn_x, h->st);
+        double2* part = h->arena.get<double2>("red_part", dot_partials());
+        double2* d_s = h->arena.get<double2>("red_out", 4);
+        dot(h->d_pn_x, nullptr, n, part, d_s, h->st);
+        double2 s;
+        SIM_CUDA(cudaMemcpyAsync(&s, d_s, sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        *phi = s.x;
+        h->pn_kept = keep != 0;
+        if (!h->pn_kept) h->arena.release("pn_X");
+        h->pn_valid = true;
+        return SIM_OK;
+    });
+}
+
+sim_status sim_projection_norm_grad(sim_handle h, double* grad_A, double* grad_B, int32_t out_on_device) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (!h->pn_valid) return fail(h, SIM_ERR_BAD_STATE, "call sim_projection_norm first");
+        if (!grad_A) return fail(h, SIM_ERR_INVALID_ARG, "grad_A is NULL");
+        const int64_t n = h->P.n;
+        const int N = (int)h->pn_z.size();
+        double2* X = h->arena.get<double2>("pn_X", (int64_t)N * n);
+        if (!h->pn_kept) {  // recompute the node solutions instead of having kept them
+            if (!solve_nodes(h, 0, h->pn_z, h->d_pn_f, 0, X))
+                return fail(h, SIM_ERR_NOT_CONVERGED, "node solve did not converge");
+        }
+        double2* d_w = h->arena.get<double2>("pn_w", 64);
+        SIM_CUDA(cudaMemcpyAsync(d_w, h->pn_w.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, h->st));
+        double2* R = h->arena.get<double2>("pn_R", (int64_t)N * n);
+        scaled_copies(h->d_pn_x, N, n, d_w, R, h->st);
+        double2* Mu = h->arena.get<double2>("pn_Mu", (int64_t)N * n);
+        if (!solve_nodes(h, 1, h->pn_z, R, n, Mu)) return fail(h, SIM_ERR_NOT_CONVERGED, "adjoint solve did not converge");
+        std::vector<double2> aA(N), aB(N);
+        for (int j = 0; j < N; ++j) {
+            aA[j] = make_double2(-2.0, 0.0);
+            aB[j] = make_double2(2.0 * h->pn_z[j].x, -2.0 * h->pn_z[j].y);
+        }
+        double2* d_a = h->arena.get<double2>("pn_a", 128);
+        SIM_CUDA(cudaMemcpyAsync(d_a, aA.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, h->st));
+        SIM_CUDA(cudaMemcpyAsync(d_a + 64, aB.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, h->st));
+        double2* gA = h->arena.get<double2>("pn_gA", h->nnzA);
+        entry_grad(entries_A(h), Mu, X, N, n, d_a, 0, gA, h->st);
+        copy_out(grad_A, gA, sizeof(double2) * h->nnzA, out_on_device, h->st);
+        if (grad_B && h->has_B) {
+            double2* gB = h->arena.get<double2>("pn_gB", h->nnzB);
+            entry_grad(entries_B(h), Mu, X, N, n, d_a + 64, 0, gB, h->st);
+            copy_out(grad_B, gB, sizeof(double2) * h->nnzB, out_on_device, h->st);
+        }
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        h->arena.release("pn_R");
+        h->arena.release("pn_Mu");
+        if (!h->pn_kept) h->arena.release("pn_X");
+        return SIM_OK;
+    });
+}
+
+sim_status sim_eigenvalue_grad(sim_handle h, double c_re, double c_im, double radius, int32_t nodes, uint64_t seed,
+                               double* lambda, double* dl_dA, double* dl_dB, int32_t out_on_device) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (!lambda || !dl_dA || !(radius > 0) || !std::isfinite(radius) || nodes < 4 || nodes > 64 ||
+            !std::isfinite(c_re) || !std::isfinite(c_im))
+            return fail(h, SIM_ERR_INVALID_ARG, "bad argument (radius > 0, 4 <= nodes <= 64, lambda and dl_dA non-NULL)");
+        const int64_t n = h->P.n;
+        std::vector<double2> z, w;
+        circle_nodes(make_double2(c_re, c_im), radius, nodes, z, w);
+        double2* vu = h->arena.get<double2>("eg_vu", 2 * n);  // v (right start), u (left start)
+        random_vectors(seed, n, 2, 0, vu, n, h->st);
+        double2* X = h->arena.get<double2>("eg_X", (int64_t)nodes * n);
+        if (!solve_nodes(h, 0, z, vu, 0, X)) return fail(h, SIM_ERR_NOT_CONVERGED, "node solve did not converge");
+        double2* d_w = h->arena.get<double2>("eg_w", 64);
+        SIM_CUDA(cudaMemcpyAsync(d_w, w.data(), sizeof(double2) * nodes, cudaMemcpyHostToDevice, h->st));
+        double2* x = h->arena.get<double2>("eg_x", n);
+        double2* y = h->arena.get<double2>("eg_y", n);
+        double2* t = h->arena.get<double2>("eg_t", n);
+        combine_nodes(X, nodes, n, d_w, false, x, h->st);
+        ensure_adjoint(h);
+        apply_B(h->Padj, vu + n, t, h->st);  // B^H u
+        if (!solve_nodes(h, 1, z, t, 0, X)) return fail(h, SIM_ERR_NOT_CONVERGED, "adjoint solve did not converge");
+        combine_nodes(X, nodes, n, d_w, true, y, h->st);
+        h->arena.release("eg_X");
+        // y^H A x and y^H B x
+        double2* part = h->arena.get<double2>("red_part", dot_partials());
+        double2* d_s = h->arena.get<double2>("red_out", 4);
+        entry_form(entries_A(h), h->P.Ka, y, x, part, d_s, h->st);
+        apply_B(h->P, x, t, h->st);
+        dot(y, t, n, part, d_s + 1, h->st);
+        double2 s[2];
+        SIM_CUDA(cudaMemcpyAsync(s, d_s, sizeof(s), cudaMemcpyDeviceToHost, h->st));
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        const double2 yAx = s[0], yBx = s[1];
+        if (!(cabsd(yBx) > 0.0)) return fail(h, SIM_ERR_INVALID_ARG, "no eigenvalue inside the circle (y^H B x = 0)");
+        const double2 lam = cdiv(yAx, yBx);
+        lambda[0] = lam.x;
+        lambda[1] = lam.y;
+        const double2 inv = cdiv(make_double2(1.0, 0.0), yBx);
+        const double2 a[2] = {inv, make_double2(-(lam.x * inv.x - lam.y * inv.y), -(lam.x * inv.y + lam.y * inv.x))};
+        double2* d_a = h->arena.get<double2>("eg_a", 2);
+        SIM_CUDA(cudaMemcpyAsync(d_a, a, sizeof(a), cudaMemcpyHostToDevice, h->st));
+        double2* gA = h->arena.get<double2>("eg_gA", h->nnzA);
+        entry_grad(entries_A(h), y, x, 1, n, d_a, 1, gA, h->st);
+        copy_out(dl_dA, gA, sizeof(double2) * h->nnzA, out_on_device, h->st);
+        if (dl_dB && h->has_B) {
+            double2* gB = h->arena.get<double2>("eg_gB", h->nnzB);
+            entry_grad(entries_B(h), y, x, 1, n, d_a + 1, 1, gB, h->st);
+            copy_out(dl_dB, gB, sizeof(double2) * h->nnzB, out_on_device, h->st);
+        }
+        SIM_CUDA(cudaStreamSynchronize(h->st));
         return SIM_OK;
     });
 }

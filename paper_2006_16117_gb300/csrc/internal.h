@@ -17,6 +17,8 @@ namespace sim {
 // that (A - σB)_ij = Ka - σ Kb.  Block-tridiagonal view: blocks of side T,
 // nb = ceil(n / T) block rows; entries of block row k fall in block columns
 // k-1, k, k+1 only (T >= the band half-width).
+struct SepCtx;  // separable.h: fast-diagonalisation preconditioner and its arena
+
 struct Pencil {
     int64_t n = 0;
     int64_t nnz = 0;
@@ -44,6 +46,10 @@ struct Pencil {
     // per row g: Lcol of its first coupling, -1 if it has none (a solve can
     // load it, and the shift's first value L0val[g], without reading Lptr first)
     const int32_t* L0col = nullptr;
+    // host pointer: when set, the inner solver's preconditioner is the
+    // fast-diagonalisation inverse of the pencil's separable part instead of
+    // the block factorisation (nothing is factored per shift)
+    SepCtx* sep = nullptr;
 };
 
 // Offset (in elements of the factor type) of Lval inside a shift's factor.
@@ -124,6 +130,10 @@ void apply_B(const Pencil& P, const double2* x, double2* y, cudaStream_t st);
 
 class DeviceArena;
 JobSpace make_jobspace(DeviceArena& ar, cudaStream_t st, int J, int k, int m, int64_t n, const std::string& tag);
+// Krylov jobs whose job spaces (vectors, basis, preconditioner work vectors)
+// fit 40% of the device's memory: the batch size of the shift and
+// multiplicity builds (at least 1).
+int max_jobs_for_memory(int64_t n, int m, int k);
 
 // ---- philox.cu ---------------------------------------------------------------
 void random_vectors(uint64_t seed, int64_t n, int k, int first, double2* out, int64_t ld, cudaStream_t st);

@@ -25,6 +25,7 @@
 #include "internal.h"
 #include "levels.h"
 #include "gs.h"
+#include "separable.h"
 #include "solve_cluster.h"
 
 namespace sim {
@@ -781,8 +782,10 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
         for (int i = 0; i < k && !act.empty(); ++i) {
             const int na = (int)act.size();
             upload_active(js, act, st);
-            if (!js.h_jobshift ||
-                !block_solve_cluster(P, opt.precision, js, act, VS_Q0 + i, vs_Z(k) + i, d_sigma, d_factor_ptrs, st))
+            if (P.sep)
+                separable_apply(P.sep->S, opt.precision, js, act, VS_Q0 + i, vs_Z(k) + i, d_sigma, *P.sep->ar, st);
+            else if (!js.h_jobshift ||
+                     !block_solve_cluster(P, opt.precision, js, act, VS_Q0 + i, vs_Z(k) + i, d_sigma, d_factor_ptrs, st))
                 throw std::runtime_error("LIMIT:block size " + std::to_string(P.T) +
                                          " too large for the cluster block solve's shared memory");
             launch_spmv(P, js, na, vs_Z(k) + i, VS_Q0 + i + 1, -1, d_sigma, st);
@@ -936,6 +939,14 @@ bool arnoldi(const Pencil& P, const sim_options& opt, JobSpace& js, const double
     }
     SIM_CUDA(cudaStreamSynchronize(st));
     return ok;
+}
+
+int max_jobs_for_memory(int64_t n, int m, int k) {
+    size_t fr = 0, tot = 0;
+    SIM_CUDA(cudaMemGetInfo(&fr, &tot));
+    const double per_job = (double)(vs_count(k) + m + 1 + 2) * (double)n * sizeof(double2);
+    const double jobs = 0.4 * (double)tot / per_job;
+    return (int)std::max(1.0, std::min(jobs, 1e6));
 }
 
 JobSpace make_jobspace(DeviceArena& ar, cudaStream_t st, int J, int k, int m, int64_t n, const std::string& tag) {

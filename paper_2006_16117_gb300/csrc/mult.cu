@@ -228,7 +228,7 @@ std::vector<int> multiplicities(const MultInput& in, bool& ok) {
         for (int c : pending) by_shift[in.shift[c]].push_back(c);
         std::vector<int> shifts;
         for (auto& kv : by_shift) shifts.push_back(kv.first);
-        const int per = std::max(1, JMAX / k);
+        const int per = std::max(1, std::min(JMAX, max_jobs_for_memory(n, m, kin)) / k);
         std::vector<int> rank_of(C, -1);
         for (size_t b0 = 0; b0 < shifts.size(); b0 += per) {
             const int nsh = (int)std::min<size_t>(per, shifts.size() - b0);

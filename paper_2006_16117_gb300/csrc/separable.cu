@@ -1,0 +1,267 @@
+// Fast-diagonalisation preconditioner (see separable.h for the formulas).
+//
+// One apply, for every active job at once:
+//   1. w = D^{-1} q            (⊗ρ_d^{-j} scaling, complex128 -> working precision)
+//   2. w = (⊗Q_d) w            (one dense mode product per axis)
+//   3. w = w / (Σ_d λ_{d,k_d} - σ b)   (denominators formed in FP64)
+//   4. w = (⊗Q_d) w
+//   5. z = D w                 (working precision -> complex128)
+// A mode product along axis d is a GEMM over the rows r = (p, q) of the
+// vector viewed as [q][j][p] with p < P = Π_{e<d} N_e and j < N_d:
+//   out(p, k, q) = Σ_j Q_d[k][j] in(p, j, q)      (Q_d symmetric).
+// Tiles of 64 rows × 64 outputs, 16 reduction steps per stage, each thread
+// 4 × 4 outputs; loads and stores are coalesced along rows for axes d > 0
+// (consecutive p) and along j / k for axis 0 (contiguous fibres).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "levels.h"
+#include "separable.h"
+
+namespace sim {
+
+namespace {
+
+// Q (both precisions), ρ^j, ρ^{-j} and λ_k of one axis.
+__global__ void k_sep_tables(int N, double2 sub, double2 dg, double2 sup, double* Q64, float* Q32, double2* rho,
+                             double2* irho, double2* lam) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t NN = (int64_t)N * N;
+    if (t < NN) {
+        const int64_t j = t / N, k = t % N;
+        // sin((j+1)(k+1)π/(N+1)) with the integer argument reduced exactly mod 2(N+1)
+        const int64_t a = ((j + 1) * (k + 1)) % (2 * (int64_t)(N + 1));
+        const double v = sqrt(2.0 / (N + 1)) * sinpi((double)a / (double)(N + 1));
+        Q64[t] = v;
+        Q32[t] = (float)v;
+    }
+    if (t < N) {
+        // ρ = sqrt(sub / sup) (principal branch); ρ^j = |r|^{j/2} e^{i j arg(r)/2}
+        const double2 r = cdiv(sub, sup);
+        const double lr = log(hypot(r.x, r.y)), ar = atan2(r.y, r.x);
+        const double j = (double)t;
+        const double mag = exp(0.5 * j * lr), ang = 0.5 * j * ar;
+        rho[t] = make_double2(mag * cos(ang), mag * sin(ang));
+        irho[t] = make_double2(cos(ang) / mag, -sin(ang) / mag);
+        const double m1 = exp(0.5 * lr), a1 = 0.5 * ar;
+        const double2 rho1 = make_double2(m1 * cos(a1), m1 * sin(a1));
+        const double2 g = cmul(sup, rho1);  // sup·ρ = sqrt(sub·sup)
+        const double c = 2.0 * cospi((double)(t + 1) / (double)(N + 1));
+        lam[t] = make_double2(dg.x + c * g.x, dg.y + c * g.y);
+    }
+}
+
+struct Axes {
+    int ndim;
+    int64_t N0, N1, N2;
+    const double2 *t0, *t1, *t2;  // per-axis tables (ρ^j, ρ^{-j} or λ)
+};
+
+__device__ __forceinline__ double2 axes_product(const Axes& a, int64_t idx) {
+    const int64_t i0 = idx % a.N0;
+    double2 v = a.t0[i0];
+    if (a.ndim > 1) {
+        const int64_t i1 = (idx / a.N0) % a.N1;
+        v = cmul(v, a.t1[i1]);
+        if (a.ndim > 2) v = cmul(v, a.t2[idx / (a.N0 * a.N1)]);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double2 axes_sum(const Axes& a, int64_t idx) {
+    const int64_t i0 = idx % a.N0;
+    double2 v = a.t0[i0];
+    if (a.ndim > 1) {
+        const int64_t i1 = (idx / a.N0) % a.N1;
+        v = cadd(v, a.t1[i1]);
+        if (a.ndim > 2) v = cadd(v, a.t2[idx / (a.N0 * a.N1)]);
+    }
+    return v;
+}
+
+template <class CW>
+__global__ void k_sep_in(JobSpace js, int in_slot, CW* W, Axes irho) {
+    const int z = blockIdx.y;
+    const int job = js.d_active[z];
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= js.n) return;
+    const double2 x = js.vec[(size_t)job * js.vstride + (size_t)in_slot * js.n + g];
+    W[(size_t)z * js.n + g] = from_c128<CW>(cmul(x, axes_product(irho, g)));
+}
+
+template <class CW>
+__global__ void k_sep_div(JobSpace js, CW* W, Axes lam, const double2* sigma, double2 b) {
+    const int z = blockIdx.y;
+    const int job = js.d_active[z];
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= js.n) return;
+    const double2 s = sigma[js.d_jobshift[job]];
+    const double2 d = csub(axes_sum(lam, g), cmul(s, b));
+    CW& w = W[(size_t)z * js.n + g];
+    w = from_c128<CW>(cdiv(to_c128(w), d));
+}
+
+template <class CW>
+__global__ void k_sep_out(JobSpace js, int out_slot, const CW* W, Axes rho) {
+    const int z = blockIdx.y;
+    const int job = js.d_active[z];
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= js.n) return;
+    js.vec[(size_t)job * js.vstride + (size_t)out_slot * js.n + g] =
+        cmul(to_c128(W[(size_t)z * js.n + g]), axes_product(rho, g));
+}
+
+constexpr int MP_BR = 64, MP_BK = 64, MP_BJ = 16, MP_THREADS = 256;
+
+// Y = mode product of X along an axis of length N with inner stride P
+// (rows r = p + P q, element (r, j) at p + P(j + N q)); Q symmetric N×N.
+template <class R, bool AXIS0>
+__global__ void __launch_bounds__(MP_THREADS) k_sep_mode(const cplx<R>* __restrict__ Xall, cplx<R>* __restrict__ Yall,
+                                                         const R* __restrict__ Q, int N, int64_t P, int64_t rows,
+                                                         int64_t n) {
+    using CW = cplx<R>;
+    __shared__ CW As[MP_BJ][MP_BR + 1];
+    __shared__ R Qs[MP_BJ][MP_BK + 1];
+    const CW* X = Xall + (size_t)blockIdx.z * n;
+    CW* Y = Yall + (size_t)blockIdx.z * n;
+    const int t = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * MP_BR;
+    const int k0 = blockIdx.y * MP_BK;
+    // compute mapping: axis 0 spreads threads over outputs k, other axes over rows
+    const int tr = AXIS0 ? t / 16 : t % 16;
+    const int tk = AXIS0 ? t % 16 : t / 16;
+    const int64_t PN = P * (int64_t)N;
+    CW acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] = mk(R(0), R(0));
+    for (int j0 = 0; j0 < N; j0 += MP_BJ) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = t + MP_THREADS * i;
+            const int jj = AXIS0 ? e % MP_BJ : e / MP_BR;
+            const int rr = AXIS0 ? e / MP_BJ : e % MP_BR;
+            const int64_t r = r0 + rr;
+            const int j = j0 + jj;
+            CW v = mk(R(0), R(0));
+            if (r < rows && j < N) v = X[(r % P) + PN * (r / P) + P * (int64_t)j];
+            As[jj][rr] = v;
+            const int kk = e % MP_BK, jq = e / MP_BK;
+            const int k = k0 + kk, jr = j0 + jq;
+            Qs[jq][kk] = (k < N && jr < N) ? Q[(size_t)jr * N + k] : R(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jj = 0; jj < MP_BJ; ++jj) {
+            CW a[4];
+            R q[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[jj][tr + 16 * i];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) q[c] = Qs[jj][tk + 16 * c];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc[i][c].x = fma(a[i].x, q[c], acc[i][c].x);
+                    acc[i][c].y = fma(a[i].y, q[c], acc[i][c].y);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + tr + 16 * i;
+        if (r >= rows) continue;
+        const int64_t base = (r % P) + PN * (r / P);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int k = k0 + tk + 16 * c;
+            if (k < N) Y[base + P * (int64_t)k] = acc[i][c];
+        }
+    }
+}
+
+Axes axes_of(const Separable& S, double2* const* tab) {
+    Axes a;
+    a.ndim = S.ndim;
+    a.N0 = S.dims[0];
+    a.N1 = S.dims[1];
+    a.N2 = S.dims[2];
+    a.t0 = tab[0];
+    a.t1 = S.ndim > 1 ? tab[1] : tab[0];
+    a.t2 = S.ndim > 2 ? tab[2] : tab[0];
+    return a;
+}
+
+template <class R>
+void apply_t(const Separable& S, const JobSpace& js, int na, int in_slot, int out_slot, const double2* d_sigma,
+             DeviceArena& ar, cudaStream_t st) {
+    using CW = cplx<R>;
+    const int64_t n = js.n;
+    CW* W0 = ar.get<CW>(sizeof(R) == 4 ? "sep_w0_f" : "sep_w0_d", (int64_t)na * n);
+    CW* W1 = ar.get<CW>(sizeof(R) == 4 ? "sep_w1_f" : "sep_w1_d", (int64_t)na * n);
+    const dim3 eg(cdiv_up(n, 256), na);
+    k_sep_in<CW><<<eg, 256, 0, st>>>(js, in_slot, W0, axes_of(S, S.irho));
+    SIM_LAUNCH_CHECK();
+    CW* cur = W0;
+    CW* nxt = W1;
+    auto modes = [&]() {
+        int64_t P = 1;
+        for (int d = 0; d < S.ndim; ++d) {
+            const int N = (int)S.dims[d];
+            const int64_t rows = n / N;
+            const R* Q = sizeof(R) == 4 ? reinterpret_cast<const R*>(S.Q32[d]) : reinterpret_cast<const R*>(S.Q64[d]);
+            const dim3 grid(cdiv_up(rows, MP_BR), cdiv_up(N, MP_BK), na);
+            if (P == 1) k_sep_mode<R, true><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
+            else k_sep_mode<R, false><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
+            SIM_LAUNCH_CHECK();
+            std::swap(cur, nxt);
+            P *= N;
+        }
+    };
+    modes();
+    k_sep_div<CW><<<eg, 256, 0, st>>>(js, cur, axes_of(S, S.lam), d_sigma, S.b);
+    SIM_LAUNCH_CHECK();
+    modes();
+    k_sep_out<CW><<<eg, 256, 0, st>>>(js, out_slot, cur, axes_of(S, S.rho));
+    SIM_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void separable_setup(Separable& S, DeviceArena& ar, cudaStream_t st, const std::string& prefix) {
+    for (int d = 0; d < S.ndim; ++d) {
+        const int64_t N = S.dims[d];
+        const std::string tag = prefix + "ax" + std::to_string(d) + "_";
+        S.Q64[d] = ar.get<double>(tag + "Q64", N * N);
+        S.Q32[d] = ar.get<float>(tag + "Q32", N * N);
+        S.rho[d] = ar.get<double2>(tag + "rho", N);
+        S.irho[d] = ar.get<double2>(tag + "irho", N);
+        S.lam[d] = ar.get<double2>(tag + "lam", N);
+        k_sep_tables<<<cdiv_up(N * N, 256), 256, 0, st>>>((int)N, S.axis[d][0], S.axis[d][1], S.axis[d][2], S.Q64[d],
+                                                         S.Q32[d], S.rho[d], S.irho[d], S.lam[d]);
+        SIM_LAUNCH_CHECK();
+    }
+    SIM_CUDA(cudaStreamSynchronize(st));
+}
+
+void separable_apply(const Separable& S, int precision, const JobSpace& js, const std::vector<int>& active,
+                     int in_slot, int out_slot, const double2* d_sigma, DeviceArena& ar, cudaStream_t st) {
+    const int na = (int)active.size();
+    if (na <= 0) return;
+    // the active list is already on the device (js.d_active) in this order
+    kprof_begin("separable", st);
+    if (precision == SIM_FP64) apply_t<double>(S, js, na, in_slot, out_slot, d_sigma, ar, st);
+    else apply_t<float>(S, js, na, in_slot, out_slot, d_sigma, ar, st);
+    double flops = 0.0;
+    for (int d = 0; d < S.ndim; ++d) flops += 2.0 * 4.0 * (double)js.n * (double)S.dims[d];  // 2 passes, 2 FMA
+    const double cw = precision == SIM_FP64 ? 16.0 : 8.0;
+    // per job: the complex128 input and output, and each pass's read and write
+    const double bytes = 32.0 * js.n + (2.0 * S.ndim + 1.0) * 2.0 * cw * js.n;
+    kprof_end("separable", st, na * bytes, na * flops);
+}
+
+}  // namespace sim

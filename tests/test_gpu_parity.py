@@ -455,3 +455,24 @@ def test_pencil_sampled_eigenvalues_by_inertia(pencil_run):
         # exactly one eigenvalue of the pencil within 2e-6 of each sampled estimate
         assert count_below(200, (1.0, 0.5), bd, x + 2e-6) - count_below(200, (1.0, 0.5), bd, x - 2e-6) == 1
 
+
+
+def test_pencil_levels_and_clusters_equal_the_oracle_record(pencil_run):
+    """The oracle's location phase on the full pencil, recorded by
+    tests/golden/make_pencil_levels.py: the same squares per level, shifts,
+    unresolvable final squares and clusters, with every estimate equal."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pencil40064_levels.json")) as fh:
+        ref = json.load(fh)
+    w, eig, mult, st = pencil_run
+    marked = st["marked_per_level"]
+    evaluated = [ref["level_counts"][0]] + [4 * m for m in marked[:-1]]
+    assert evaluated == ref["level_counts"]
+    assert st["num_shifts"] == ref["num_shifts"]
+    assert st["final_squares"] == ref["final_squares"] == marked[-1]
+    assert st["unresolvable_final"] == ref["unresolvable_final"]
+    est = np.array(ref["estimate_re"]) + 1j * np.array(ref["estimate_im"])
+    assert eig.size == est.size == ref["clusters"]
+    assert np.max(np.abs(eig - est)) <= 1e-9

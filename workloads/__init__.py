@@ -15,6 +15,9 @@ from .pencils import (  # noqa: F401
     Csr,
     cd2d_csr,
     cd2d_eigenvalues,
+    cdr_axes,
+    cdr_csr,
+    cdr_separable_eigenvalues,
     tridiag_toeplitz_csr,
     jordan_csr,
     pair_blocks_csr,
@@ -24,4 +27,4 @@ from .pencils import (  # noqa: F401
     dense_to_csr,
     complex_gaussian,
 )
-from .configs import config_small, config_pencil, config_jordan_small, Workload  # noqa: F401
+from .configs import config_small, config_pencil, config_jordan_small, config_cdr2d, config_cdr3d, Workload  # noqa: F401

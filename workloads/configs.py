@@ -28,6 +28,9 @@ import numpy as np
 from .pencils import (
     Csr,
     block_diag_csr,
+    cdr_axes,
+    cdr_csr,
+    cdr_separable_eigenvalues,
     cd2d_csr,
     cd2d_eigenvalues,
     complex_gaussian,
@@ -49,6 +52,7 @@ class Workload:
     expected_count: int | None = None   # Σ multiplicities inside R, from closed forms / inertia
     reference_eigs: np.ndarray | None = None  # closed-form eigenvalues inside R, when known
     reference_mult: np.ndarray | None = None
+    separable: tuple | None = None  # (dims, (sub, diag, sup) per axis) of a separable principal part
 
 
 def window_region(lam_sorted_real: np.ndarray, start: int, count: int, im=(-0.3, 0.7)):
@@ -154,4 +158,60 @@ def config_jordan_small(seed: int = 0, sup: float = JORDAN_SUP) -> Workload:
         options=dict(m=50, n0=4, delta0=0.05, eps=1e-8, h0=1e-6),
         expected_count=int(inside.size + 4 * je.size),
         reference_eigs=eigs[order], reference_mult=mult[order],
+    )
+
+
+# ---------------------------------------------------------------------------
+# separable-principal-part workloads: 2-D and 3-D convection–diffusion–reaction
+# ---------------------------------------------------------------------------
+def _low_end_window(lam_real: np.ndarray, count: int, spread: float) -> tuple[int, float, float]:
+    """Left edge below the smallest eigenvalue and a right edge in the first gap
+    after `count` eigenvalues wide enough for a perturbation moving each
+    eigenvalue by at most `spread` to the right; returns (count, lo, hi)."""
+    lr = np.sort(lam_real)
+    c = count
+    while lr[c] - lr[c - 1] <= spread + 1.0:
+        c += 1
+    return c, float(lr[0] - 2.0), float(0.5 * (lr[c - 1] + spread + lr[c]))
+
+
+def config_cdr2d(N: int = 500, count: int = 20, seed: int = 0) -> Workload:
+    """2-D convection–diffusion–reaction -Δu + (1, 0.5)·∇u + c u on an N×N grid
+    (n = N², 250,000 at N = 500), c_i ~ U[0,1] (seed 5), B = I: similar to a
+    symmetric matrix with 0 <= c <= 1 added, so every eigenvalue is real and
+    lies within [0, 1] to the right of one of the closed-form eigenvalues of
+    the separable part.  The region spans the low end of the spectrum up to a
+    gap, holding `count` or a few more eigenvalues, with Im range [-0.3, 0.7]."""
+    beta = (1.0, 0.5)
+    c = np.random.default_rng(5).uniform(0.0, 1.0, N * N)
+    A = cdr_csr((N, N), beta, c)
+    lam = cdr_separable_eigenvalues((N, N), beta)
+    cnt, lo, hi = _low_end_window(lam.real, count, 1.0)
+    return Workload(
+        name="cdr2d-%dx%d reaction U[0,1] (n=%d, %d eigenvalues)" % (N, N, N * N, cnt),
+        A=A, B=None, region=(lo, hi, -0.3, 0.7), f=complex_gaussian(A.n, seed),
+        options=dict(m=50, n0=4, delta0=0.05, eps=1e-8, h0=1e-6),
+        expected_count=cnt,
+        separable=((N, N), cdr_axes((N, N), beta)),
+    )
+
+
+def config_cdr3d(N: int = 100, width: float = 140.0, seed: int = 0, at: float = 0.25) -> Workload:
+    """3-D convection–diffusion–reaction -Δu + (1, 0.5, 0.25)·∇u + r u on an
+    N×N×N grid (n = N³, 10⁶ at N = 100), r_i = sqrt(U) e^{2πiV} uniform in the
+    unit disk (seed 4), B = I.  The region is `width` units of Re centred on the
+    point a fraction `at` along the separable part's spectrum, Im [-1.3, 1.7]."""
+    beta = (1.0, 0.5, 0.25)
+    rng = np.random.default_rng(4)
+    U, V = rng.uniform(size=N**3), rng.uniform(size=N**3)
+    r = np.sqrt(U) * np.exp(2j * np.pi * V)
+    A = cdr_csr((N, N, N), beta, r)
+    lam = cdr_separable_eigenvalues((N, N, N), beta).real
+    mid = float(lam.min() + at * (lam.max() - lam.min()))
+    region = (mid - 0.5 * width, mid + 0.5 * width, -1.3, 1.7)
+    return Workload(
+        name="cdr3d-%d^3 complex reaction in the unit disk (n=%d), Re width %g" % (N, N**3, width),
+        A=A, B=None, region=region, f=complex_gaussian(A.n, seed),
+        options=dict(m=50, n0=4, delta0=0.05, eps=1e-8, h0=1e-6, init_side=1.0),
+        separable=((N, N, N), cdr_axes((N, N, N), beta)),
     )
