@@ -231,6 +231,58 @@ sim_status sim_projection(sim_handle h, int64_t c, double* out);
  * SIM_ERR_NOT_CONVERGED (a Hessenberg QR iteration hit its sweep limit). */
 sim_status sim_refine(sim_handle h, double* out, int32_t* refined, int64_t capacity, int64_t* count);
 
+/* ---- Differentiation -------------------------------------------------------
+ * Gradients of spectral functionals with respect to the values of A's and B's
+ * stored entries (the order of the CSR arrays given to sim_create), through
+ * adjoint shifted solves with (A - zB)^H.  The paper defines the spectral
+ * projection these functionals are built on (Sec. 2, Eq. XLXf) but does not
+ * differentiate it.  The shifted systems are solved by the inner solver
+ * (FGMRES with the handle's preconditioner: a block factorisation per node,
+ * or the separable one of sim_set_separable).  These calls do not depend on
+ * the region state and leave it alone. */
+
+/* Φ = ||P f||² with P f = Σ_j w_j (A - z_j B)^{-1} f, the trapezoid rule of
+ * Eq. XLXf on the circle z_j = c + r e^{2πij/N}, w_j = (z_j - c)/N (j < N =
+ * nodes, 4..64).  f: complex128[n], host or device (f_on_device).  keep != 0
+ * keeps the N node solutions on the device for sim_projection_norm_grad
+ * (N·n·16 bytes); keep == 0 frees them, and the gradient call solves for them
+ * again (less memory, N more solves).  Errors: SIM_ERR_INVALID_ARG,
+ * SIM_ERR_NOT_CONVERGED, SIM_ERR_OOM, SIM_ERR_CUDA. */
+sim_status sim_projection_norm(sim_handle h, double c_re, double c_im, double radius, int32_t nodes, const double* f,
+                               int32_t f_on_device, int32_t keep, double* phi);
+
+/* The gradient of the last sim_projection_norm's Φ: with the adjoint solves
+ * (A - z_j B)^H μ_j = conj(w_j) P f,
+ *   grad_A[e] = -2 Σ_j μ_j[p] conj(x_j[q]),   grad_B[e] = 2 Σ_j conj(z_j) μ_j[p] conj(x_j[q])
+ * for stored entry e at (p, q), where x_j = (A - z_j B)^{-1} f; each value is
+ * ∂Φ/∂Re(entry) + i ∂Φ/∂Im(entry) (complex128, nnz_A resp. nnz_B values).
+ * grad_B may be NULL (and is ignored when B = I).  out_on_device selects
+ * device or host output arrays.  Errors: SIM_ERR_BAD_STATE (no forward call),
+ * SIM_ERR_INVALID_ARG, SIM_ERR_NOT_CONVERGED, SIM_ERR_CUDA. */
+sim_status sim_projection_norm_grad(sim_handle h, double* grad_A, double* grad_B, int32_t out_on_device);
+
+/* A simple eigenvalue λ inside the circle (c, r) and its derivatives
+ * dλ/dA[e] = conj(y_p) x_q / (y^H B x), dλ/dB[e] = -λ conj(y_p) x_q / (y^H B x)
+ * (complex128 per stored entry; λ is holomorphic in the entries).  x and y
+ * are the right and left eigenvectors from the same quadrature as above: x =
+ * Σ_j w_j (A - z_j B)^{-1} v and y = Σ_j conj(w_j) (A - z_j B)^{-H} B^H u for
+ * Philox4x64-10 vectors v, u (key (seed, 0x53494D4D), indices 0 and 1);
+ * lambda (2 doubles) = y^H A x / y^H B x.  The circle must hold exactly one
+ * eigenvalue, simple; the quadrature error is about (r/d)^N for the nearest
+ * other eigenvalue at distance d from c.  dl_dB may be NULL.
+ * Errors: SIM_ERR_INVALID_ARG (bad argument, or no eigenvalue inside),
+ * SIM_ERR_NOT_CONVERGED, SIM_ERR_OOM, SIM_ERR_CUDA. */
+sim_status sim_eigenvalue_grad(sim_handle h, double c_re, double c_im, double radius, int32_t nodes, uint64_t seed,
+                               double* lambda, double* dl_dA, double* dl_dB, int32_t out_on_device);
+
+/* Replaces the values of A's (a_values, nnz_A complex128) and/or B's
+ * (b_values, nnz_B) stored entries, keeping the sparsity patterns given to
+ * sim_create; either may be NULL.  The handle returns to its created state
+ * (region, shifts and factorisations discarded); a separable preconditioner
+ * stays (B must remain a multiple of I).  Errors: SIM_ERR_INVALID_ARG
+ * (non-finite values, b_values with B = I), SIM_ERR_OOM, SIM_ERR_CUDA. */
+sim_status sim_update_values(sim_handle h, const double* a_values, const double* b_values, int32_t on_device);
+
 /* Copies the counters into *out (size = sizeof(sim_stats_t)). */
 sim_status sim_stats(sim_handle h, sim_stats_t* out, size_t size);
 

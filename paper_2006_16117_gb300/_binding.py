@@ -64,7 +64,8 @@ EXPORTS = [
     "sim_multiplicity", "sim_refine", "sim_projection", "sim_stats", "sim_last_error", "sim_destroy", "sim_shift_count", "sim_get_shift",
     "sim_eval_squares", "sim_apply_shifted", "sim_shifted_solve", "sim_random_vectors",
     "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count", "sim_apply_shifted_noalloc",
-    "sim_set_separable",
+    "sim_set_separable", "sim_projection_norm", "sim_projection_norm_grad", "sim_eigenvalue_grad",
+    "sim_update_values",
 ]
 
 
@@ -82,6 +83,10 @@ def lib():
     L.sim_create.argtypes = [C.POINTER(SimCsr), C.POINTER(SimCsr), C.POINTER(SimOptions), vp, C.POINTER(vp)]
     L.sim_set_region.argtypes = [vp, dbl, dbl, dbl, dbl, vp, i32, u64]
     L.sim_set_separable.argtypes = [vp, i32, vp, vp]
+    L.sim_projection_norm.argtypes = [vp, dbl, dbl, dbl, i32, vp, i32, i32, C.POINTER(dbl)]
+    L.sim_projection_norm_grad.argtypes = [vp, vp, vp, i32]
+    L.sim_eigenvalue_grad.argtypes = [vp, dbl, dbl, dbl, i32, u64, vp, vp, vp, i32]
+    L.sim_update_values.argtypes = [vp, vp, vp, i32]
     L.sim_solve_level.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
     L.sim_eigenvalues.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.sim_multiplicity.argtypes = [vp, vp, i64, C.POINTER(i64)]
@@ -205,6 +210,62 @@ class Sim:
         a = np.ascontiguousarray(np.asarray(axes, dtype=np.complex128).reshape(-1))
         assert a.size == 3 * d.size
         _check(lib().sim_set_separable(self.h, int(d.size), d.ctypes.data, a.ctypes.data), self.h)
+
+    def _vec_arg(self, v):
+        """(pointer, on_device, keep-alive) of a complex128 vector: a CUDA
+        tensor is passed as a device pointer, anything else as host memory."""
+        if hasattr(v, "data_ptr") and v.is_cuda:
+            return v.data_ptr(), 1, v
+        a = np.ascontiguousarray(v, dtype=np.complex128)
+        return a.ctypes.data, 0, a
+
+    def projection_norm(self, center, radius, f, nodes=16, keep=True):
+        """Φ = ||P f||² on the circle (center, radius) (sim_projection_norm)."""
+        ptr, dev, _keep = self._vec_arg(f)
+        phi = C.c_double()
+        _check(lib().sim_projection_norm(self.h, float(np.real(center)), float(np.imag(center)), float(radius),
+                                         int(nodes), ptr, dev, 1 if keep else 0, C.byref(phi)), self.h)
+        return phi.value
+
+    def projection_norm_grad(self, nnz_A, nnz_B=0, device=False):
+        """Gradients of the last projection_norm's Φ on A's (and B's) stored
+        entries, ∂Φ/∂Re + i ∂Φ/∂Im; torch CUDA tensors if device else numpy."""
+        if device:
+            import torch
+
+            gA = torch.empty(nnz_A, dtype=torch.complex128, device="cuda")
+            gB = torch.empty(max(nnz_B, 1), dtype=torch.complex128, device="cuda")
+            _check(lib().sim_projection_norm_grad(self.h, gA.data_ptr(), gB.data_ptr() if nnz_B else None, 1), self.h)
+            return gA, (gB if nnz_B else None)
+        gA = np.zeros(nnz_A, dtype=np.complex128)
+        gB = np.zeros(max(nnz_B, 1), dtype=np.complex128)
+        _check(lib().sim_projection_norm_grad(self.h, gA.ctypes.data, gB.ctypes.data if nnz_B else None, 0), self.h)
+        return gA, (gB if nnz_B else None)
+
+    def eigenvalue_grad(self, center, radius, nnz_A, nnz_B=0, nodes=16, seed=0x5EED, device=False):
+        """A simple eigenvalue inside (center, radius) and dλ/dA, dλ/dB on the
+        stored entries (sim_eigenvalue_grad)."""
+        lam = np.zeros(2)
+        if device:
+            import torch
+
+            dA = torch.empty(nnz_A, dtype=torch.complex128, device="cuda")
+            dB = torch.empty(max(nnz_B, 1), dtype=torch.complex128, device="cuda")
+            pa, pb = dA.data_ptr(), (dB.data_ptr() if nnz_B else None)
+        else:
+            dA = np.zeros(nnz_A, dtype=np.complex128)
+            dB = np.zeros(max(nnz_B, 1), dtype=np.complex128)
+            pa, pb = dA.ctypes.data, (dB.ctypes.data if nnz_B else None)
+        _check(lib().sim_eigenvalue_grad(self.h, float(np.real(center)), float(np.imag(center)), float(radius),
+                                         int(nodes), int(seed), lam.ctypes.data, pa, pb, 1 if device else 0), self.h)
+        return complex(lam[0], lam[1]), dA, (dB if nnz_B else None)
+
+    def update_values(self, a_values=None, b_values=None):
+        """New values on A's / B's stored entries (same patterns)."""
+        pa = self._vec_arg(a_values) if a_values is not None else (None, 0, None)
+        pb = self._vec_arg(b_values) if b_values is not None else (None, 0, None)
+        dev = pa[1] if a_values is not None else pb[1]
+        _check(lib().sim_update_values(self.h, pa[0], pb[0], dev), self.h)
 
     def set_region(self, region, f=None, seed=0):
         re_lo, re_hi, im_lo, im_hi = (float(x) for x in region)

@@ -88,6 +88,7 @@ struct sim_ctx {
     int64_t nnzA = 0, nnzB = 0;
     int32_t *d_arow = nullptr, *d_acol = nullptr, *d_amap = nullptr;
     int32_t *d_brow = nullptr, *d_bcol = nullptr, *d_bmap = nullptr;
+    std::vector<int32_t> h_amap, h_bmap;
     // adjoint pencil (A^H, B^H), built on first use by the gradient calls
     Pencil Padj;
     bool adj_built = false;
@@ -653,6 +654,7 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
             h->d_arow = (int32_t*)up_buf(h.get(), "A_row", row.data(), sizeof(int32_t) * row.size());
             h->d_acol = (int32_t*)up_buf(h.get(), "A_col", a.ci.data(), sizeof(int32_t) * a.ci.size());
             h->d_amap = (int32_t*)up_buf(h.get(), "A_map", amap.data(), sizeof(int32_t) * amap.size());
+            h->h_amap = amap;
             if (hasB) {
                 std::vector<int32_t> brow(b.ci.size());
                 for (int64_t i = 0; i < n; ++i)
@@ -661,6 +663,7 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
                 h->d_brow = (int32_t*)up_buf(h.get(), "B_row", brow.data(), sizeof(int32_t) * brow.size());
                 h->d_bcol = (int32_t*)up_buf(h.get(), "B_col", b.ci.data(), sizeof(int32_t) * b.ci.size());
                 h->d_bmap = (int32_t*)up_buf(h.get(), "B_map", bmap.data(), sizeof(int32_t) * bmap.size());
+                h->h_bmap = bmap;
             }
         }
         SIM_CUDA(cudaStreamSynchronize(h->st));
@@ -1313,6 +1316,74 @@ sim_status sim_eigenvalue_grad(sim_handle h, double c_re, double c_im, double ra
             copy_out(dl_dB, gB, sizeof(double2) * h->nnzB, out_on_device, h->st);
         }
         SIM_CUDA(cudaStreamSynchronize(h->st));
+        return SIM_OK;
+    });
+}
+
+sim_status sim_update_values(sim_handle h, const double* a_values, const double* b_values, int32_t on_device) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (!a_values && !b_values) return fail(h, SIM_ERR_INVALID_ARG, "no values given");
+        if (b_values && !h->has_B) return fail(h, SIM_ERR_INVALID_ARG, "the handle has B = I");
+        const auto kind = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        std::vector<double2> va, vb;
+        if (a_values) {
+            va.resize(h->nnzA);
+            SIM_CUDA(cudaMemcpy(va.data(), a_values, sizeof(double2) * h->nnzA, kind));
+        }
+        if (b_values) {
+            vb.resize(h->nnzB);
+            SIM_CUDA(cudaMemcpy(vb.data(), b_values, sizeof(double2) * h->nnzB, kind));
+        }
+        for (const auto& v : va)
+            if (!std::isfinite(v.x) || !std::isfinite(v.y)) return fail(h, SIM_ERR_INVALID_ARG, "non-finite value");
+        for (const auto& v : vb)
+            if (!std::isfinite(v.x) || !std::isfinite(v.y)) return fail(h, SIM_ERR_INVALID_ARG, "non-finite value");
+        std::vector<double2> Ka = h->u_Ka, Kb = h->u_Kb;
+        for (size_t i = 0; i < va.size(); ++i) Ka[h->h_amap[i]] = va[i];
+        for (size_t i = 0; i < vb.size(); ++i) Kb[h->h_bmap[i]] = vb[i];
+        // B's kind (identity, diagonal, general) and diagonal from the new values
+        const int64_t n = h->P.n;
+        int b_kind = 0;
+        std::vector<double2> bd(n, make_double2(h->has_B ? 0.0 : 1.0, 0.0));
+        if (h->has_B) {
+            b_kind = 1;
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t e = h->u_rp[i]; e < h->u_rp[i + 1]; ++e) {
+                    if (h->u_ci[e] == i) bd[i] = Kb[e];
+                    else if (Kb[e].x != 0 || Kb[e].y != 0) b_kind = 2;
+                }
+        }
+        bool b_scalar = b_kind == 0;
+        if (b_kind == 1) {
+            b_scalar = true;
+            for (int64_t i = 1; i < n && b_scalar; ++i) b_scalar = bd[i].x == bd[0].x && bd[i].y == bd[0].y;
+        }
+        if (h->sep && !b_scalar) return fail(h, SIM_ERR_INVALID_ARG, "the separable preconditioner needs B = b I");
+        SepCtx* sep = h->P.sep;
+        upload_pencil(h->arena, h->st, h->P, h->u_rp, h->u_ci, Ka, Kb, b_kind, bd, "P_");
+        h->P.sep = sep;
+        h->u_Ka.swap(Ka);
+        h->u_Kb.swap(Kb);
+        h->u_bd.swap(bd);
+        h->b_scalar = b_scalar;
+        h->b_value = b_kind == 0 ? make_double2(1.0, 0.0) : h->u_bd[0];
+        if (h->sep && (h->sep->S.b.x != h->b_value.x || h->sep->S.b.y != h->b_value.y)) {
+            h->sep->S.b = h->b_value;
+        }
+        // everything derived from the old values is stale
+        h->adj_built = false;
+        h->sep_adj.reset();
+        h->Padj.sep = nullptr;
+        h->pn_valid = false;
+        for (int s = 0; s < h->cap; ++s) {
+            if (h->factors[s]) {
+                cudaFree(h->factors[s]);
+                h->factors[s] = nullptr;
+            }
+        }
+        h->S = 0;
+        h->state = ST_CREATED;
         return SIM_OK;
     });
 }

@@ -159,3 +159,34 @@ def test_simm_cdr3d_separable_matches_oracle(simlib, cdr3d_small, precision):
     assert eig.size == ref.eigenvalues.size
     assert np.max(np.abs(eig - ref.eigenvalues)) <= 1e-6
     assert np.array_equal(mult, ref.multiplicities)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_simm_cdr2d_full_size_matches_oracle_record(simlib, precision):
+    """n = 250,000 (the 2-D convection–diffusion–reaction workload at full
+    size): levels, shifts, eigenvalues and multiplicities equal to the
+    oracle's run recorded by tests/golden/make_cdr2d_record.py."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "cdr2d500_record.json")) as fh:
+        ref = json.load(fh)
+    w = config_cdr2d()
+    opt = simlib.sim_default_options(precision=precision, **w.options)
+    s = simlib.Sim(w.A, None, opt)
+    try:
+        s.set_separable(*w.separable)
+        s.set_region(w.region, w.f)
+        marked = s.solve_all_levels()
+        eig = s.eigenvalues()
+        mult = s.multiplicity()
+        st = s.stats()
+    finally:
+        s.close()
+    assert [ref["level_counts"][0]] + [4 * m for m in marked[:-1]] == ref["level_counts"]
+    assert st["num_shifts"] == ref["num_shifts"]
+    est = np.array(ref["estimate_re"]) + 1j * np.array(ref["estimate_im"])
+    assert eig.size == est.size == w.expected_count
+    assert np.max(np.abs(eig - est)) <= 1e-9
+    assert np.array_equal(mult, ref["multiplicity"])
