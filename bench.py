@@ -38,9 +38,11 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 path (0 skips it)")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 path (0 skips it)")
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the secondary workloads (2-D and 3-D convection-diffusion-reaction, 64-pencil batch)")
     p.add_argument("--region-width", type=float, default=0.0,
                    help="profiling aid: keep only the left part of the region, this many units wide")
     return p.parse_args()
@@ -148,14 +150,6 @@ def workload(rank: int, width: float = 0.0):
     return w
 
 
-def one_step(sim, s, w):
-    s.set_region(w.region, w.f_dev)
-    s.solve_all_levels()
-    eig = s.eigenvalues()
-    mult = s.multiplicity()
-    return eig, mult
-
-
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -191,7 +185,10 @@ def cpu_baseline(w_full):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": located / dt, "unit": "eigenvalues/s", "cores": cores, "kind": "oracle",
             "sample": "Re[%.3f, %.3f] x Im[%.1f, %.1f] of the n=40,064 pencil: %d eigenvalues (with multiplicity) "
-                      "in %.1f s; NumPy/SciPy FP64, SuperLU single-threaded, BLAS on the listed cores"
+                      "in %.1f s; NumPy/SciPy FP64, SuperLU single-threaded, BLAS on the listed cores. A bounded "
+                      "slice: the full region's location phase alone (steps 1-6, no multiplicity) took the oracle "
+                      "606.7 s on a development host (tests/golden/pencil40064_levels.json), so the full-region "
+                      "rate is lower than this slice's"
                       % (region[0], region[1], im_lo, im_hi, located, dt),
             "seconds": dt, "located": located}
 
@@ -226,6 +223,147 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+KERNELS = ("block_solve", "factor", "gram_schmidt", "eval_level", "spmv", "separable")
+
+
+def kernel_roofline(kstats, peaks, src, fp64_tflops, precision):
+    """Roofline of the dominant kernel of an instrumented pass: bytes- or
+    flop-bound by the kernel's arithmetic (the FP64 streaming kernels are
+    bound by the measured FP64 FMA rate, see the DESIGN roofline table)."""
+    ks = {k: v for k, v in kstats.items() if v}
+    if not ks:
+        return None, {}
+    top = max(ks, key=lambda k: ks[k]["ms"])
+    k = ks[top]
+    per = {"avg_launch_ms": k["ms"] / max(1, k["launches"]), "launches": k["launches"]}
+    hbm_bound = top in ("block_solve", "factor", "spmv") and precision == "mixed" or top == "separable"
+    if top == "block_solve" and precision == "mixed":
+        achieved = k["bytes"] / (k["ms"] / 1000.0) / 1e9
+        line = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": traffic_record(top, precision, k["bytes"] / max(1, k["launches"])),
+                "peak_source": src, "bytes_per_launch": k["bytes"] / max(1, k["launches"])}
+    elif hbm_bound:
+        achieved = k["bytes"] / (k["ms"] / 1000.0) / 1e9
+        line = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "bytes_per_launch": k["bytes"] / max(1, k["launches"])}
+    else:
+        achieved = k["flops"] / (k["ms"] / 1000.0) / 1e12
+        line = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp64_tflops if fp64_tflops else None, "traffic": None,
+                "peak_source": "measured FP64 FMA rate of this GPU (sim_measure_fma_peak)",
+                "flops_per_launch": k["flops"] / max(1, k["launches"])}
+    line.update(per)
+    table = {kk: {"ms": v["ms"], "launches": v["launches"],
+                  "GB/s": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["bytes"] else None,
+                  "TFLOP/s": v["flops"] / (v["ms"] / 1000.0) / 1e12}
+             for kk, v in ks.items()}
+    return line, table
+
+
+def timed_steps(torch, sim, handle, step, warmup, steps, stream, world, local, clocks=False):
+    """warmup untimed steps, then `steps` timed with CUDA events on the
+    library's stream between barriers; units summed over ranks, time max."""
+    for _ in range(warmup):
+        step(handle)
+    torch.cuda.synchronize()
+    ck = Clocks(local) if clocks else None
+    if ck:
+        ck.start()
+    launches0 = sim.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    located, solves, last = 0, 0, None
+    for _ in range(steps):
+        last = step(handle)
+        located += last["located"]
+        solves += last["solves"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = barrier_max(ev0.elapsed_time(ev1), world)
+    return {"ms_total": ms, "steps": steps, "located": int(allreduce_sum(located, world)),
+            "solves": int(allreduce_sum(solves, world)), "launches": sim.launch_count() - launches0,
+            "last": last, "clocks": ck.stop() if ck else None}
+
+
+def instrumented_pass(sim, handle, step):
+    """One more step with per-kernel CUDA-event timing (kept out of the timed
+    steps: the events add host work per launch)."""
+    sim.kernel_timing(True)
+    step(handle)
+    ks = {k: sim.kernel_stats(k) for k in KERNELS}
+    sim.kernel_timing(False)
+    return ks
+
+
+def single_step_fn(sim, w, f):
+    def step(s):
+        s.set_region(w.region, f)
+        s.solve_all_levels()
+        eig = s.eigenvalues()
+        mult = s.multiplicity()
+        st = s.stats()
+        return {"located": int(mult.sum()), "solves": int(st["inner_solves"]), "eig": eig, "mult": mult,
+                "stats": st}
+    return step
+
+
+def secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64_tflops):
+    """The other configurations, measured with fewer steps (1 warm-up, 1 timed;
+    the workload, not the step count, is what they show)."""
+    from workloads.configs import config_batch, config_cdr2d, config_cdr3d
+
+    out = {}
+    for name, make in (("cdr2d_250k", lambda: config_cdr2d()), ("cdr3d_1m_subregion", lambda: config_cdr3d(100, 15.0))):
+        w = make()
+        f = torch.from_numpy(w.f).to(torch.device("cuda", local))
+        s = sim.Sim(w.A, None, sim.sim_default_options(precision="mixed", **w.options), stream=stream)
+        s.set_separable(*w.separable)
+        step = single_step_fn(sim, w, f)
+        r = timed_steps(torch, sim, s, step, 1, 1, stream, world, local)
+        ks = instrumented_pass(sim, s, step)
+        roof, table = kernel_roofline(ks, peaks, src, fp64_tflops, "mixed")
+        st = r["last"]["stats"]
+        out[name] = {"workload": w.name, "region": list(w.region), "value": r["located"] / (r["ms_total"] / 1000.0),
+                     "unit": "eigenvalues/s", "ms_per_step": r["ms_total"], "warmup": 1, "steps": 1,
+                     "located": r["located"], "expected": w.expected_count, "shifts": int(st["num_shifts"]),
+                     "shifted_solves_per_s": r["solves"] / (r["ms_total"] / 1000.0),
+                     "gmres_iters_per_solve": st["gmres_iterations"] / max(1, st["inner_solves"]),
+                     "loose_inner_solves": int(st["loose_inner_solves"]),
+                     "preconditioner": "separable (fast diagonalisation), complex64 mode products",
+                     "roofline": roof, "kernels": table}
+        s.close()
+        del w
+    b = config_batch()
+    opt = sim.sim_default_options(precision="mixed", **b.pencils[0].options)
+    bt = sim.Batch([w.A for w in b.pencils], None, opt, stream=stream)
+    for p, w in enumerate(b.pencils):
+        bt.set_separable(p, *w.separable)
+    regions = [w.region for w in b.pencils]
+    fs = [w.f for w in b.pencils]
+
+    def bstep(h):
+        h.set_regions(regions, fs)
+        h.solve_all_levels()
+        loc = sum(int(h.multiplicity(p).sum()) for p in range(h.count))
+        sol = sum(int(h.stats(p)["inner_solves"]) for p in range(h.count))
+        return {"located": loc, "solves": sol}
+
+    r = timed_steps(torch, sim, bt, bstep, 1, 1, stream, world, local)
+    out["batch_64"] = {"workload": b.name, "value": r["located"] / (r["ms_total"] / 1000.0), "unit": "eigenvalues/s",
+                       "ms_per_step": r["ms_total"], "warmup": 1, "steps": 1, "located": r["located"],
+                       "expected": b.expected_count, "pencils": len(b.pencils),
+                       "n_total": int(sum(w.A.n for w in b.pencils)),
+                       "shifted_solves_per_s": r["solves"] / (r["ms_total"] / 1000.0),
+                       "level_evaluation": "every pencil's squares of a level in one launch (sim_batch_solve_level)"}
+    bt.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -239,55 +377,27 @@ def run_ours(args, world, rank, local):
     A, B = w.A, w.B
     dA = (torch.from_numpy(A.indptr).to(dev), torch.from_numpy(A.indices).to(dev), torch.from_numpy(A.data).to(dev))
     dB = (torch.from_numpy(B.indptr).to(dev), torch.from_numpy(B.indices).to(dev), torch.from_numpy(B.data).to(dev))
-    w.f_dev = torch.from_numpy(w.f).to(dev)
+    f_dev = torch.from_numpy(w.f).to(dev)
     torch.cuda.synchronize()
-
-    def make(precision):
-        return sim.Sim(dA, dB, sim.sim_default_options(precision=precision, **w.options), stream=stream)
+    fp64_tflops = sim.measure_fma_peak(True)
+    fp32_tflops = sim.measure_fma_peak(False)
+    peaks, src = measured_peaks()
+    step = single_step_fn(sim, w, f_dev)
 
     results = {}
-    for precision, steps in (("mixed", args.steps), ("fp64", args.fp64_steps)):
+    for precision, steps, warm in (("mixed", args.steps, args.warmup), ("fp64", args.fp64_steps, 1)):
         if steps <= 0:
             continue
-        s = make(precision)
-        for _ in range(args.warmup if precision == "mixed" else 1):
-            one_step(sim, s, w)
-        torch.cuda.synchronize()
-        clocks = Clocks(local)
+        s = sim.Sim(dA, dB, sim.sim_default_options(precision=precision, **w.options), stream=stream)
+        rec = timed_steps(torch, sim, s, step, warm, steps, stream, world, local, clocks=(precision == "mixed"))
         if precision == "mixed":
-            sim.kernel_timing(True)
-            clocks.start()
-        launches0 = sim.launch_count()
-        barrier(world)
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        located, solves = 0, 0
-        for _ in range(steps):
-            eig, mult = one_step(sim, s, w)
-            located += int(mult.sum())
-            solves += s.stats()["inner_solves"]
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        ms = ev0.elapsed_time(ev1)
-        ms_max = barrier_max(ms, world)
-        located = int(allreduce_sum(located, world))  # all ranks' units
-        solves = int(allreduce_sum(solves, world))
-        rec = {"ms_total": ms_max, "steps": steps, "located": located, "solves": solves,
-               "launches": sim.launch_count() - launches0, "eig": eig, "mult": mult, "stats": s.stats()}
-        if precision == "mixed":
-            rec["clocks"] = clocks.stop()
-            rec["kernels"] = {k: sim.kernel_stats(k)
-                              for k in ("block_solve", "factor", "gram_schmidt", "eval_level", "spmv")}
-            sim.kernel_timing(False)
+            rec["kernels"] = instrumented_pass(sim, s, step)
         results[precision] = rec
         s.close()
 
     # end to end through the public API from pinned host buffers
     def pinned(a):
-        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        return t
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
 
     hA = tuple(pinned(x) for x in (A.indptr, A.indices, A.data.view(np.float64)))
     hB = tuple(pinned(x) for x in (B.indptr, B.indices, B.data.view(np.float64)))
@@ -321,6 +431,10 @@ def run_ours(args, world, rank, local):
     e2e_t = barrier_max(sum(e2e_times), world)
     e2e_located = int(allreduce_sum(e2e_located, world))
 
+    secondary = None
+    if not args.no_secondary and world == 1:
+        secondary = secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64_tflops)
+
     if rank != 0:
         return
     mixed = results["mixed"]
@@ -349,46 +463,36 @@ def run_ours(args, world, rank, local):
         },
         "shifted_solves_per_s": mixed["solves"] / (mixed["ms_total"] / 1000.0),
         "e2e": {"value": e2e_located / e2e_t if e2e_t > 0 else None, "unit": "eigenvalues/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times)},
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed.get("clocks"),
     }
-    st = mixed["stats"]
+    st = mixed["last"]["stats"]
     line["quality"] = {"located_per_step": mixed["located"] // (mixed["steps"] * world),  # per rank
                        "expected": w.expected_count,
                        "clusters": int(st["clusters"]), "shifts": int(st["num_shifts"]),
                        "max_inner_residual": st["max_inner_residual"],
-                       "gmres_iters_per_solve": st["gmres_iterations"] / max(1, st["inner_solves"])}
+                       "loose_inner_solves": int(st["loose_inner_solves"]),
+                       "gmres_iters_per_solve": st["gmres_iterations"] / max(1, st["inner_solves"]),
+                       "shift_retries": int(st["shift_retries"])}
     if "fp64" in results:
         f = results["fp64"]
         fv = f["located"] / (f["ms_total"] / 1000.0)
         line["fp64"] = {"value": fv, "unit": "eigenvalues/s", "ms_per_step": f["ms_total"] / f["steps"],
+                        "steps": f["steps"], "warmup": 1,
                         "shifted_solves_per_s": f["solves"] / (f["ms_total"] / 1000.0)}
         line["mixed_over_fp64"] = value / fv
-        if f["eig"].size == mixed["eig"].size:
-            line["quality"]["max_abs_diff_mixed_vs_fp64"] = float(np.max(np.abs(f["eig"] - mixed["eig"])))
-    # roofline of the dominant kernel (live CUDA-event timing over the timed steps)
-    ks = {k: v for k, v in mixed["kernels"].items() if v}
-    peaks, src = measured_peaks()
-    top = max(ks, key=lambda k: ks[k]["ms"])
-    k = ks[top]
-    if top in ("block_solve", "gram_schmidt", "factor"):
-        achieved = k["bytes"] / (k["ms"] / 1000.0) / 1e9
-        line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                            "traffic": traffic_record(top, "mixed", k["bytes"] / max(1, k["launches"])),
-                            "peak_source": src,
-                            "avg_launch_ms": k["ms"] / max(1, k["launches"]),
-                            "bytes_per_launch": k["bytes"] / max(1, k["launches"])}
-    else:
-        line["roofline"] = {"kernel": top, "bound": "alu", "achieved": k["flops"] / (k["ms"] / 1000.0) / 1e12,
-                            "peak": 1.25, "unit": "TFLOP/s", "frac": k["flops"] / (k["ms"] / 1000.0) / 1.25e12,
-                            "traffic": None, "peak_source": "nominal FP64"}
-    line["kernels"] = {kk: {"ms": v["ms"], "launches": v["launches"],
-                            "GB/s": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["bytes"] else None,
-                            "TFLOP/s": v["flops"] / (v["ms"] / 1000.0) / 1e12}
-                       for kk, v in ks.items()}
-    line["kernels_total_ms"] = sum(v["ms"] for v in ks.values())
+        fe, me = f["last"]["eig"], mixed["last"]["eig"]
+        if fe.size == me.size:
+            line["quality"]["max_abs_diff_mixed_vs_fp64"] = float(np.max(np.abs(fe - me)))
+    # roofline of the dominant kernel, from the instrumented pass (live CUDA events)
+    roof, table = kernel_roofline(mixed["kernels"], peaks, src, fp64_tflops, "mixed")
+    line["roofline"] = roof
+    line["kernels"] = table
+    line["kernels_total_ms"] = sum(v["ms"] for v in table.values())
+    line["measured_fma_peaks_tflops"] = {"fp64": fp64_tflops, "fp32": fp32_tflops}
+    if secondary is not None:
+        line["secondary"] = secondary
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
         line["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}

@@ -128,6 +128,8 @@ typedef struct {
     double t_factor_ms, t_krylov_ms, t_levels_ms, t_merge_ms, t_mult_ms;
     int64_t loose_inner_solves;          /* inner solves that stagnated above inner_tol and were
                                             accepted within 100·inner_tol */
+    int64_t unresolvable_last_level;     /* squares of the last solved level no shift resolved */
+    int64_t shift_retries;               /* evaluations against a second, third, ... shift (summed) */
 } sim_stats_t;
 
 /* Fills *opt with the defaults listed above.  opt must not be NULL. */
@@ -231,6 +233,40 @@ sim_status sim_projection(sim_handle h, int64_t c, double* out);
  * SIM_ERR_NOT_CONVERGED (a Hessenberg QR iteration hit its sweep limit). */
 sim_status sim_refine(sim_handle h, double* out, int32_t* refined, int64_t capacity, int64_t* count);
 
+/* ---- Batches of pencils ------------------------------------------------------
+ * Many independent pencils, each with its own region, located together: the
+ * squares of every pencil's current level are evaluated in one launch (the
+ * level-synchronous evaluation of all squares that Sec. 3.3 makes the
+ * parallel axis), and subdivided by one compaction.  Each pencil's shifts,
+ * Krylov spaces, merge and multiplicity stay its own; a square only uses its
+ * own pencil's shifts.  Pencils may differ in size; their regions must give
+ * the same number of levels (same initial side and h0).  A batch owns one
+ * sim_handle per pencil (sim_batch_handle), all on the given stream. */
+typedef struct sim_batch_ctx* sim_batch;
+
+/* count pencils A[p] (and B[p]; B == NULL means B = I for all), one set of
+ * options.  Errors as sim_create (the message of sim_batch_last_error(NULL)
+ * names the pencil). */
+sim_status sim_batch_create(int32_t count, const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream,
+                            sim_batch* out);
+/* sim_set_separable for pencil p. */
+sim_status sim_batch_set_separable(sim_batch b, int32_t p, int32_t ndim, const int64_t* dims, const double* axes);
+/* Steps 1-3 of Sec. 3.5 for every pencil: regions[4p..4p+3] = (re_lo, re_hi,
+ * im_lo, im_hi); f[p] = host complex128[n_p] or f == NULL (Philox, key word 0
+ * = seed + p).  Errors: as sim_set_region; SIM_ERR_INVALID_ARG when the
+ * regions need different numbers of levels. */
+sim_status sim_batch_set_regions(sim_batch b, const double* regions, const double* const* f, uint64_t seed);
+/* One level of every pencil in one evaluation launch (Sec. 3.3, step 5);
+ * *n_marked: marked squares over all pencils; *done = 1 after the last level.
+ * Then sim_batch_eigenvalues / sim_batch_multiplicity per pencil. */
+sim_status sim_batch_solve_level(sim_batch b, int64_t* n_marked, int32_t* done);
+sim_status sim_batch_eigenvalues(sim_batch b, int32_t p, double* out, int64_t capacity, int64_t* count);
+sim_status sim_batch_multiplicity(sim_batch b, int32_t p, int32_t* out, int64_t capacity, int64_t* count);
+/* Pencil p's handle (owned by the batch): for sim_stats, sim_refine, ... */
+sim_handle sim_batch_handle(sim_batch b, int32_t p);
+const char* sim_batch_last_error(sim_batch b);
+void sim_batch_destroy(sim_batch b);
+
 /* ---- Differentiation -------------------------------------------------------
  * Gradients of spectral functionals with respect to the values of A's and B's
  * stored entries (the order of the CSR arrays given to sim_create), through
@@ -316,6 +352,18 @@ sim_status sim_eval_squares(const double* H, int32_t m, int32_t m_eff, double be
                             double sig_im, const double* centers, const double* sides, int64_t count,
                             int32_t residual_scale, double* indicator, double* rho, void* stream);
 
+/* Sec. 3.2, Eqs. zjHm and rmLc1: with the eigendecomposition H_m = P D P^{-1}
+ * of shift s's Hessenberg matrix (computed on the GPU: QR eigenvalues, one
+ * step of inverse iteration per eigenvector, c_1 = P^{-1} e_1), the last
+ * entry of the projected solution at each point z_j costs O(m):
+ *   e_m^T y_j = β r_m (I + (σ - z_j) D)^{-1} c_1,   r_m = e_m^T P,
+ * and so does the residual |σ - z_j| h_{m+1,m} |e_m^T y_j| / β of Eq. eq:error
+ * (relative to β).  z: count complex128 points (host); ym: complex128[count]
+ * and rho: double[count] (host outputs).  Exact for a diagonalisable H_m; the
+ * rounding grows with the condition of P.  Valid after sim_set_region.
+ * Errors: SIM_ERR_BAD_STATE, SIM_ERR_INVALID_ARG, SIM_ERR_NOT_CONVERGED. */
+sim_status sim_residual_screen(sim_handle h, int32_t s, const double* z, int64_t count, double* ym, double* rho);
+
 /* y = (A - σB) x for the handle's pencil (complex128[n] vectors). */
 sim_status sim_apply_shifted(sim_handle h, double sig_re, double sig_im, const double* x, double* y);
 
@@ -361,6 +409,10 @@ sim_status sim_random_vectors(uint64_t seed, int64_t n, int32_t k, int32_t first
  * sim_launch_count returns the number of kernel launches the library has made
  * in this process. */
 void sim_kernel_timing(int32_t enable);
+/* A measured arithmetic peak of the current device, for the benchmark's
+ * rooflines: which = 0 FP64 fused multiply-add throughput, 1 FP32; writes
+ * TFLOP/s (2 flops per FMA) to *tflops.  Runs one short register-only kernel. */
+sim_status sim_measure_fma_peak(int32_t which, double* tflops);
 int32_t sim_kernel_stats(const char* name, double* ms, double* bytes, double* flops, int64_t* launches);
 int64_t sim_launch_count(void);
 

@@ -151,6 +151,31 @@ def projected_solve(ks: KrylovSpace, z, scale: str = "solution"):
     return y, rho
 
 
+def eig_decomposition(ks: KrylovSpace):
+    """Sec. 3.2, Eq. zjHm: H_m = P D P^{-1}.  Returns the eigenvalues d, the
+    eigenvector matrix P, c_1 = P^{-1} e_1 and r_m = e_m^T P (the last row)."""
+    m = ks.m_eff
+    d, P = np.linalg.eig(ks.H[:m, :m])
+    e1 = np.zeros(m, dtype=np.complex128)
+    e1[0] = 1.0
+    c1 = np.linalg.solve(P, e1)
+    return d, P, c1, P[m - 1, :].copy()
+
+
+def screened_last_entry(ks: KrylovSpace, z, dec=None):
+    """Sec. 3.2, Eq. rmLc1: e_m^T y_j = β r_m (I + (σ - z_j)D)^{-1} c_1, O(m) per
+    point z_j once H_m's eigendecomposition is known (exact for a
+    diagonalisable H_m; its rounding grows with the condition of P).  Returns
+    e_m^T y for each z and the β-relative residual |σ - z| h_{m+1,m} |e_m^T y| / β
+    of Eq. eq:error."""
+    d, P, c1, rm = dec if dec is not None else eig_decomposition(ks)
+    z = np.asarray(z, dtype=np.complex128)
+    alpha = ks.sigma - z
+    ym = ks.beta * np.sum(rm * c1 / (1.0 + alpha[..., None] * d), axis=-1)
+    hlast = float(abs(ks.H[ks.m_eff, ks.m_eff - 1]))
+    return ym, np.abs(alpha) * hlast * np.abs(ym) / ks.beta
+
+
 # ---------------------------------------------------------------------------
 # Quadrature on the circle circumscribing a square, and the indicator
 # ---------------------------------------------------------------------------

@@ -15,12 +15,14 @@ from ._binding import (  # noqa: F401
     SimOptions,
     SimStats,
     Sim,
+    Batch,
     eval_squares,
     lib,
     library_path,
     random_vectors,
     kernel_timing,
     kernel_stats,
+    measure_fma_peak,
     launch_count,
     sim_default_options,
     run,

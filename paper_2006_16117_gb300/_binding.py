@@ -50,7 +50,7 @@ class SimStats(C.Structure):
         ("unresolvable_final", C.c_int64), ("final_squares", C.c_int64), ("clusters", C.c_int64),
         ("max_inner_residual", C.c_double), ("t_factor_ms", C.c_double), ("t_krylov_ms", C.c_double),
         ("t_levels_ms", C.c_double), ("t_merge_ms", C.c_double), ("t_mult_ms", C.c_double),
-        ("loose_inner_solves", C.c_int64),
+        ("loose_inner_solves", C.c_int64), ("unresolvable_last_level", C.c_int64), ("shift_retries", C.c_int64),
     ]
 
     def as_dict(self):
@@ -65,7 +65,10 @@ EXPORTS = [
     "sim_eval_squares", "sim_apply_shifted", "sim_shifted_solve", "sim_random_vectors",
     "sim_kernel_timing", "sim_kernel_stats", "sim_launch_count", "sim_apply_shifted_noalloc",
     "sim_set_separable", "sim_projection_norm", "sim_projection_norm_grad", "sim_eigenvalue_grad",
-    "sim_update_values",
+    "sim_update_values", "sim_measure_fma_peak",
+    "sim_batch_create", "sim_batch_set_separable", "sim_batch_set_regions", "sim_batch_solve_level",
+    "sim_batch_eigenvalues", "sim_batch_multiplicity", "sim_batch_handle", "sim_batch_last_error",
+    "sim_batch_destroy", "sim_residual_screen",
 ]
 
 
@@ -87,6 +90,20 @@ def lib():
     L.sim_projection_norm_grad.argtypes = [vp, vp, vp, i32]
     L.sim_eigenvalue_grad.argtypes = [vp, dbl, dbl, dbl, i32, u64, vp, vp, vp, i32]
     L.sim_update_values.argtypes = [vp, vp, vp, i32]
+    L.sim_measure_fma_peak.argtypes = [i32, C.POINTER(dbl)]
+    L.sim_residual_screen.argtypes = [vp, i32, vp, i64, vp, vp]
+    L.sim_batch_create.argtypes = [i32, C.POINTER(SimCsr), C.POINTER(SimCsr), C.POINTER(SimOptions), vp, C.POINTER(vp)]
+    L.sim_batch_set_separable.argtypes = [vp, i32, i32, vp, vp]
+    L.sim_batch_set_regions.argtypes = [vp, vp, vp, u64]
+    L.sim_batch_solve_level.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
+    L.sim_batch_eigenvalues.argtypes = [vp, i32, vp, i64, C.POINTER(i64)]
+    L.sim_batch_multiplicity.argtypes = [vp, i32, vp, i64, C.POINTER(i64)]
+    L.sim_batch_handle.argtypes = [vp, i32]
+    L.sim_batch_handle.restype = vp
+    L.sim_batch_last_error.argtypes = [vp]
+    L.sim_batch_last_error.restype = C.c_char_p
+    L.sim_batch_destroy.argtypes = [vp]
+    L.sim_batch_destroy.restype = None
     L.sim_solve_level.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
     L.sim_eigenvalues.argtypes = [vp, vp, i64, C.POINTER(i64)]
     L.sim_multiplicity.argtypes = [vp, vp, i64, C.POINTER(i64)]
@@ -348,6 +365,16 @@ class Sim:
                self.h)
         return complex(sig[0], sig[1]), H.T.copy(), float(beta[0]), me.value
 
+    def residual_screen(self, s, z):
+        """e_m^T y and the β-relative residual at points z from shift s's
+        eigendecomposition (Sec. 3.2, sim_residual_screen)."""
+        z = np.ascontiguousarray(z, dtype=np.complex128)
+        ym = np.zeros(z.size, dtype=np.complex128)
+        rho = np.zeros(z.size)
+        _check(lib().sim_residual_screen(self.h, int(s), z.ctypes.data, z.size, ym.ctypes.data, rho.ctypes.data),
+               self.h)
+        return ym, rho
+
     def apply_shifted(self, sigma, x):
         import torch
 
@@ -364,6 +391,89 @@ class Sim:
         _check(lib().sim_shifted_solve(self.h, float(np.real(sigma)), float(np.imag(sigma)), r.data_ptr(),
                                        x.data_ptr(), C.byref(it), C.byref(rel)), self.h)
         return x, it.value, rel.value
+
+
+def _bcheck(status, b):
+    if status != 0:
+        msg = lib().sim_batch_last_error(b)
+        raise SimError(status, msg.decode() if msg else "")
+
+
+class Batch:
+    """Owns one sim_batch (include/sim.h): many pencils located together, every
+    pencil's squares of a level evaluated in one launch."""
+
+    def __init__(self, As, Bs=None, options: SimOptions | None = None, stream=None):
+        L = lib()
+        self._A = [_as_csr(a) for a in As]
+        self._B = [_as_csr(b) for b in Bs] if Bs is not None else None
+        arrA = (SimCsr * len(As))(*[a.c for a in self._A])
+        arrB = (SimCsr * len(As))(*[b.c for b in self._B]) if self._B is not None else None
+        self.options = options if options is not None else sim_default_options()
+        h = C.c_void_p()
+        _bcheck(L.sim_batch_create(len(As), arrA, arrB, C.byref(self.options), _stream_ptr(stream), C.byref(h)), None)
+        self.h = h
+        self.count = len(As)
+        self.n = [a.c.n for a in self._A]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_separable(self, p, dims, axes):
+        d = np.ascontiguousarray(dims, dtype=np.int64)
+        a = np.ascontiguousarray(np.asarray(axes, dtype=np.complex128).reshape(-1))
+        _bcheck(lib().sim_batch_set_separable(self.h, int(p), int(d.size), d.ctypes.data, a.ctypes.data), self.h)
+
+    def set_regions(self, regions, fs=None, seed=0):
+        r = np.ascontiguousarray(np.asarray(regions, dtype=np.float64).reshape(-1))
+        assert r.size == 4 * self.count
+        if fs is None:
+            ptr = None
+        else:
+            self._f = [np.ascontiguousarray(f, dtype=np.complex128) for f in fs]
+            arr = (C.c_void_p * self.count)(*[f.ctypes.data for f in self._f])
+            self._farr = arr
+            ptr = C.cast(arr, C.c_void_p)
+        _bcheck(lib().sim_batch_set_regions(self.h, r.ctypes.data, ptr, int(seed)), self.h)
+
+    def solve_all_levels(self):
+        counts = []
+        while True:
+            nm, done = C.c_int64(), C.c_int32()
+            _bcheck(lib().sim_batch_solve_level(self.h, C.byref(nm), C.byref(done)), self.h)
+            counts.append(nm.value)
+            if done.value:
+                return counts
+
+    def eigenvalues(self, p) -> np.ndarray:
+        cnt = C.c_int64()
+        _bcheck(lib().sim_batch_eigenvalues(self.h, int(p), None, 0, C.byref(cnt)), self.h)
+        out = np.zeros(cnt.value, dtype=np.complex128)
+        if cnt.value:
+            _bcheck(lib().sim_batch_eigenvalues(self.h, int(p), out.ctypes.data, cnt.value, C.byref(cnt)), self.h)
+        return out
+
+    def multiplicity(self, p) -> np.ndarray:
+        cnt = C.c_int64()
+        _bcheck(lib().sim_batch_multiplicity(self.h, int(p), None, 0, C.byref(cnt)), self.h)
+        out = np.zeros(cnt.value, dtype=np.int32)
+        if cnt.value:
+            _bcheck(lib().sim_batch_multiplicity(self.h, int(p), out.ctypes.data, cnt.value, C.byref(cnt)), self.h)
+        return out
+
+    def stats(self, p) -> dict:
+        s = SimStats()
+        hp = lib().sim_batch_handle(self.h, int(p))
+        _check(lib().sim_stats(hp, C.byref(s), C.sizeof(s)), hp)
+        return s.as_dict()
 
 
 def run(A, B, region, f, options: SimOptions | None = None, multiplicity=True, stream=None):
@@ -409,6 +519,13 @@ def kernel_stats(name: str):
     if not lib().sim_kernel_stats(name.encode(), C.byref(ms), C.byref(by), C.byref(fl), C.byref(ln)):
         return None
     return {"ms": ms.value, "bytes": by.value, "flops": fl.value, "launches": ln.value}
+
+
+def measure_fma_peak(fp64: bool = True) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
+    v = C.c_double()
+    _check(lib().sim_measure_fma_peak(0 if fp64 else 1, C.byref(v)), None)
+    return v.value
 
 
 def launch_count() -> int:

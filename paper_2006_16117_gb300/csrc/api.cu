@@ -518,6 +518,60 @@ void copy_out(void* dst, const void* src, size_t bytes, int on_device, cudaStrea
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------
+// batches of pencils: every pencil's squares of a level in one evaluation
+// ---------------------------------------------------------------------------
+struct sim_batch_ctx {
+    cudaStream_t st = nullptr;
+    std::string err;
+    std::vector<sim_ctx*> h;
+    DeviceArena arena;
+    bool region = false;
+    int K = 1, level = 1, cur = 0;
+    int64_t nsq = 0;
+    std::vector<int> sb;         // first global shift id of each pencil (+ total at the end)
+    std::vector<double> re_lo, im_lo, s1;
+    int64_t squares_evaluated = 0;
+    ~sim_batch_ctx() {
+        for (sim_ctx* x : h) delete x;
+    }
+};
+
+namespace {
+
+sim_status bfail(sim_batch_ctx* b, sim_status s, const std::string& msg) {
+    if (b) b->err = msg;
+    return s;
+}
+
+template <class F> sim_status bguarded(sim_batch_ctx* b, F&& f) {
+    try {
+        b->err.clear();
+        return f();
+    } catch (const CudaError& e) {
+        return bfail(b, e.code == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA, e.what);
+    } catch (const std::bad_alloc&) {
+        return bfail(b, SIM_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        const std::string w = e.what();
+        if (w.rfind("LIMIT:", 0) == 0) return bfail(b, SIM_ERR_LIMIT, w.substr(6));
+        return bfail(b, SIM_ERR_CUDA, w);
+    }
+}
+
+__global__ void k_add_offset(const int* in, int* out, int64_t n, int off) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] + off;
+}
+
+__global__ void k_fill_int(int* out, int64_t n, int v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v;
+}
+
+}  // namespace
+
 // Accessors for sim_apply_shifted_noalloc (noalloc.cu).
 namespace sim {
 struct NoallocView {
@@ -858,12 +912,21 @@ sim_status sim_solve_level(sim_handle h, int64_t* n_marked, int32_t* done) {
         la.re_lo = h->re_lo;
         la.im_lo = h->im_lo;
         la.side = side;
+        la.retries = h->arena.get<unsigned long long>("retries", 1);
+        SIM_CUDA(cudaMemsetAsync(la.retries, 0, sizeof(unsigned long long), h->st));
         eval_level(shift_table(h), la, 0, h->st);
         h->stats.squares_evaluated += N;
-        h->stats.projected_solves += 8 * N;
         const int nbk = cdiv_up(std::max<int64_t>(N, 1), 1024);
         int64_t* bsum = h->arena.get<int64_t>("bsum", nbk + 1);
         int64_t* tot = h->arena.get<int64_t>("tot", 1);
+        h->stats.unresolvable_last_level = count_marked(flag, N, bsum, tot, h->arena.host_i64(), h->st);
+        {
+            unsigned long long rt = 0;
+            SIM_CUDA(cudaMemcpyAsync(&rt, la.retries, sizeof(rt), cudaMemcpyDeviceToHost, h->st));
+            SIM_CUDA(cudaStreamSynchronize(h->st));
+            h->stats.shift_retries += (int64_t)rt;
+            h->stats.projected_solves += 8 * (N + (int64_t)rt);
+        }
         const int64_t cnt = count_marked(mark, N, bsum, tot, h->arena.host_i64(), h->st);
         const bool last = (k == h->K);
         if (!last) {
@@ -1384,6 +1447,277 @@ sim_status sim_update_values(sim_handle h, const double* a_values, const double*
         }
         h->S = 0;
         h->state = ST_CREATED;
+        return SIM_OK;
+    });
+}
+
+// ---- batches of pencils -------------------------------------------------------
+sim_status sim_batch_create(int32_t count, const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream,
+                            sim_batch* out) {
+    if (!out) return SIM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 1 || !A) return SIM_ERR_INVALID_ARG;
+    std::unique_ptr<sim_batch_ctx> b(new sim_batch_ctx());
+    b->st = (cudaStream_t)stream;
+    for (int p = 0; p < count; ++p) {
+        sim_handle h = nullptr;
+        const sim_status s = sim_create(&A[p], B ? &B[p] : nullptr, opt, stream, &h);
+        if (s != SIM_OK) {
+            g_create_error = "pencil " + std::to_string(p) + ": " + g_create_error;
+            return s;
+        }
+        b->h.push_back(h);
+    }
+    *out = b.release();
+    return SIM_OK;
+}
+
+sim_status sim_batch_set_separable(sim_batch b, int32_t p, int32_t ndim, const int64_t* dims, const double* axes) {
+    if (!b) return SIM_ERR_INVALID_ARG;
+    if (p < 0 || p >= (int)b->h.size()) return bfail(b, SIM_ERR_INVALID_ARG, "pencil index out of range");
+    const sim_status s = sim_set_separable(b->h[p], ndim, dims, axes);
+    if (s != SIM_OK) b->err = "pencil " + std::to_string(p) + ": " + b->h[p]->err;
+    b->region = false;
+    return s;
+}
+
+sim_status sim_batch_set_regions(sim_batch b, const double* regions, const double* const* f, uint64_t seed) {
+    if (!b) return SIM_ERR_INVALID_ARG;
+    return bguarded(b, [&]() -> sim_status {
+        if (!regions) return bfail(b, SIM_ERR_INVALID_ARG, "regions is NULL");
+        const int P = (int)b->h.size();
+        b->region = false;
+        b->sb.assign(1, 0);
+        b->re_lo.clear();
+        b->im_lo.clear();
+        b->s1.clear();
+        for (int p = 0; p < P; ++p) {
+            sim_ctx* h = b->h[p];
+            const double* r = regions + 4 * p;
+            const sim_status s = sim_set_region(h, r[0], r[1], r[2], r[3], f ? f[p] : nullptr, 0, seed + p);
+            if (s != SIM_OK) return bfail(b, s, "pencil " + std::to_string(p) + ": " + h->err);
+            if (p > 0 && h->K != b->h[0]->K)
+                return bfail(b, SIM_ERR_INVALID_ARG, "the pencils' regions need the same number of levels");
+            b->sb.push_back(b->sb.back() + h->S);
+            b->re_lo.push_back(h->re_lo);
+            b->im_lo.push_back(h->im_lo);
+            b->s1.push_back(h->s1);
+        }
+        const int S = b->sb.back();  // every pencil has at most max_shifts <= SIM_MAX_SHIFTS - 1
+        const int m = b->h[0]->opt.m;
+        // the batch's shift table: every pencil's Krylov data at its offset
+        double2* H = b->arena.get<double2>("H", (int64_t)S * (m + 1) * m);
+        double* beta = b->arena.get<double>("beta", S);
+        int* meff = b->arena.get<int>("meff", S);
+        double2* sigma = b->arena.get<double2>("sigma", S);
+        int* pen = b->arena.get<int>("pencil_of", S);
+        int64_t N = 0;
+        for (int p = 0; p < P; ++p) N += b->h[p]->nsq;
+        int64_t* ix = b->arena.get<int64_t>("L0_ix", N);
+        int64_t* iy = b->arena.get<int64_t>("L0_iy", N);
+        int* sid = b->arena.get<int>("L0_sid", N);
+        int64_t at = 0;
+        for (int p = 0; p < P; ++p) {
+            sim_ctx* h = b->h[p];
+            const int o = b->sb[p], Sp = h->S;
+            SIM_CUDA(cudaMemcpyAsync(H + (size_t)o * (m + 1) * m, h->d_H, sizeof(double2) * Sp * (m + 1) * m,
+                                     cudaMemcpyDeviceToDevice, b->st));
+            SIM_CUDA(cudaMemcpyAsync(beta + o, h->d_beta, sizeof(double) * Sp, cudaMemcpyDeviceToDevice, b->st));
+            SIM_CUDA(cudaMemcpyAsync(meff + o, h->d_meff, sizeof(int) * Sp, cudaMemcpyDeviceToDevice, b->st));
+            SIM_CUDA(cudaMemcpyAsync(sigma + o, h->d_sigma, sizeof(double2) * Sp, cudaMemcpyDeviceToDevice, b->st));
+            k_fill_int<<<cdiv_up(Sp, 256), 256, 0, b->st>>>(pen + o, Sp, p);
+            SIM_LAUNCH_CHECK();
+            const int64_t n0 = h->nsq;
+            SIM_CUDA(cudaMemcpyAsync(ix + at, h->arena.get<int64_t>("L0_ix", n0), sizeof(int64_t) * n0,
+                                     cudaMemcpyDeviceToDevice, b->st));
+            SIM_CUDA(cudaMemcpyAsync(iy + at, h->arena.get<int64_t>("L0_iy", n0), sizeof(int64_t) * n0,
+                                     cudaMemcpyDeviceToDevice, b->st));
+            k_add_offset<<<cdiv_up(n0, 256), 256, 0, b->st>>>(h->arena.get<int>("L0_sid", n0), sid + at, n0, o);
+            SIM_LAUNCH_CHECK();
+            at += n0;
+        }
+        std::vector<int> psb(b->sb.begin(), b->sb.end() - 1), pse(b->sb.begin() + 1, b->sb.end());
+        SIM_CUDA(cudaMemcpyAsync(b->arena.get<int>("p_sb", P), psb.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(b->arena.get<int>("p_se", P), pse.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(b->arena.get<double>("p_re_lo", P), b->re_lo.data(), sizeof(double) * P,
+                                 cudaMemcpyHostToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(b->arena.get<double>("p_im_lo", P), b->im_lo.data(), sizeof(double) * P,
+                                 cudaMemcpyHostToDevice, b->st));
+        SIM_CUDA(cudaStreamSynchronize(b->st));
+        b->K = b->h[0]->K;
+        b->level = 1;
+        b->cur = 0;
+        b->nsq = N;
+        b->squares_evaluated = 0;
+        b->region = true;
+        return SIM_OK;
+    });
+}
+
+sim_status sim_batch_solve_level(sim_batch b, int64_t* n_marked, int32_t* done) {
+    if (!b) return SIM_ERR_INVALID_ARG;
+    return bguarded(b, [&]() -> sim_status {
+        if (!b->region || b->level > b->K) return bfail(b, SIM_ERR_BAD_STATE, "no level to solve");
+        const int P = (int)b->h.size();
+        const int k = b->level;
+        const sim_ctx* h0 = b->h[0];
+        std::vector<double> side(P);
+        for (int p = 0; p < P; ++p) side[p] = b->s1[p] / std::ldexp(1.0, k - 1);
+        double* d_side = b->arena.get<double>("p_side", P);
+        SIM_CUDA(cudaMemcpyAsync(d_side, side.data(), sizeof(double) * P, cudaMemcpyHostToDevice, b->st));
+        ShiftTable t;
+        t.H = b->arena.get<double2>("H", 1);
+        t.beta = b->arena.get<double>("beta", 1);
+        t.meff = b->arena.get<int>("meff", 1);
+        t.sigma = b->arena.get<double2>("sigma", 1);
+        t.S = b->sb.back();
+        t.m = h0->opt.m;
+        t.scale = h0->opt.residual_scale;
+        t.eps = h0->opt.eps;
+        t.delta0 = h0->opt.delta0;
+        t.pencil_of = b->arena.get<int>("pencil_of", 1);
+        t.p_re_lo = b->arena.get<double>("p_re_lo", 1);
+        t.p_im_lo = b->arena.get<double>("p_im_lo", 1);
+        t.p_side = d_side;
+        t.p_sb = b->arena.get<int>("p_sb", 1);
+        t.p_se = b->arena.get<int>("p_se", 1);
+        const std::string a = "L" + std::to_string(b->cur) + "_", c = "L" + std::to_string(1 - b->cur) + "_";
+        const int64_t N = b->nsq;
+        int64_t* ix = b->arena.get<int64_t>(a + "ix", N);
+        int64_t* iy = b->arena.get<int64_t>(a + "iy", N);
+        int* sid = b->arena.get<int>(a + "sid", N);
+        uint8_t* mark = b->arena.get<uint8_t>("mark", N);
+        uint8_t* flag = b->arena.get<uint8_t>("flag", N);
+        LevelArgs la;
+        la.ix = ix;
+        la.iy = iy;
+        la.sid = sid;
+        la.mark = mark;
+        la.flag = flag;
+        la.ind = b->arena.get<double>("ind", N);
+        la.count = N;
+        eval_level(t, la, 0, b->st);
+        b->squares_evaluated += N;
+        const int nbk = cdiv_up(std::max<int64_t>(N, 1), 1024);
+        int64_t* bsum = b->arena.get<int64_t>("bsum", nbk + 1);
+        int64_t* tot = b->arena.get<int64_t>("tot", 1);
+        const int64_t cnt = count_marked(mark, N, bsum, tot, b->arena.host_i64(), b->st);
+        const bool last = k == b->K;
+        if (!last) {
+            if (4 * cnt > h0->opt.max_squares)
+                return bfail(b, SIM_ERR_LIMIT, "level " + std::to_string(k + 1) + " would hold " +
+                                                   std::to_string(4 * cnt) + " squares (> max_squares)");
+            emit_marked(mark, flag, ix, iy, sid, N, bsum, 0, b->arena.get<int64_t>(c + "ix", 4 * cnt),
+                        b->arena.get<int64_t>(c + "iy", 4 * cnt), b->arena.get<int>(c + "sid", 4 * cnt), nullptr,
+                        b->st);
+            b->cur = 1 - b->cur;
+            b->nsq = 4 * cnt;
+        } else {
+            // the final squares, pencil by pencil (the list stays in pencil order),
+            // go to each pencil's handle with its own shift ids
+            int64_t* fix = b->arena.get<int64_t>("F_ix", cnt);
+            int64_t* fiy = b->arena.get<int64_t>("F_iy", cnt);
+            int* fsid = b->arena.get<int>("F_sid", cnt);
+            uint8_t* ffl = b->arena.get<uint8_t>("F_flag", cnt);
+            emit_marked(mark, flag, ix, iy, sid, N, bsum, 1, fix, fiy, fsid, ffl, b->st);
+            std::vector<int> hs(cnt);
+            if (cnt) SIM_CUDA(cudaMemcpyAsync(hs.data(), fsid, sizeof(int) * cnt, cudaMemcpyDeviceToHost, b->st));
+            SIM_CUDA(cudaStreamSynchronize(b->st));
+            int64_t at = 0;
+            for (int p = 0; p < P; ++p) {
+                sim_ctx* h = b->h[p];
+                int64_t e = at;
+                while (e < cnt && hs[e] < b->sb[p + 1]) ++e;
+                const int64_t np = e - at;
+                if (np) {
+                    SIM_CUDA(cudaMemcpyAsync(h->arena.get<int64_t>("F_ix", np), fix + at, sizeof(int64_t) * np,
+                                             cudaMemcpyDeviceToDevice, b->st));
+                    SIM_CUDA(cudaMemcpyAsync(h->arena.get<int64_t>("F_iy", np), fiy + at, sizeof(int64_t) * np,
+                                             cudaMemcpyDeviceToDevice, b->st));
+                    SIM_CUDA(cudaMemcpyAsync(h->arena.get<uint8_t>("F_flag", np), ffl + at, np,
+                                             cudaMemcpyDeviceToDevice, b->st));
+                    k_add_offset<<<cdiv_up(np, 256), 256, 0, b->st>>>(fsid + at, h->arena.get<int>("F_sid", np), np,
+                                                                      -b->sb[p]);
+                    SIM_LAUNCH_CHECK();
+                }
+                h->nfinal = np;
+                h->s_final = b->s1[p] / std::ldexp(1.0, k - 1);
+                h->level = k + 1;
+                h->stats.levels_done = k;
+                h->state = ST_LEVELS_DONE;
+                at = e;
+            }
+            SIM_CUDA(cudaStreamSynchronize(b->st));
+            b->region = false;
+        }
+        b->level = k + 1;
+        if (n_marked) *n_marked = cnt;
+        if (done) *done = last ? 1 : 0;
+        return SIM_OK;
+    });
+}
+
+sim_status sim_batch_eigenvalues(sim_batch b, int32_t p, double* out, int64_t capacity, int64_t* count) {
+    if (!b) return SIM_ERR_INVALID_ARG;
+    if (p < 0 || p >= (int)b->h.size()) return bfail(b, SIM_ERR_INVALID_ARG, "pencil index out of range");
+    const sim_status s = sim_eigenvalues(b->h[p], out, capacity, count);
+    if (s != SIM_OK) b->err = b->h[p]->err;
+    return s;
+}
+
+sim_status sim_batch_multiplicity(sim_batch b, int32_t p, int32_t* out, int64_t capacity, int64_t* count) {
+    if (!b) return SIM_ERR_INVALID_ARG;
+    if (p < 0 || p >= (int)b->h.size()) return bfail(b, SIM_ERR_INVALID_ARG, "pencil index out of range");
+    const sim_status s = sim_multiplicity(b->h[p], out, capacity, count);
+    if (s != SIM_OK) b->err = b->h[p]->err;
+    return s;
+}
+
+sim_handle sim_batch_handle(sim_batch b, int32_t p) {
+    if (!b || p < 0 || p >= (int)b->h.size()) return nullptr;
+    return b->h[p];
+}
+
+const char* sim_batch_last_error(sim_batch b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void sim_batch_destroy(sim_batch b) { delete b; }
+
+sim_status sim_residual_screen(sim_handle h, int32_t s, const double* z, int64_t count, double* ym, double* rho) {
+    if (!h) return fail(nullptr, SIM_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> sim_status {
+        if (h->state < ST_REGION || h->S < 1) return fail(h, SIM_ERR_BAD_STATE, "no Krylov spaces (call sim_set_region)");
+        if (s < 0 || s >= h->S) return fail(h, SIM_ERR_INVALID_ARG, "shift index out of range");
+        if (count < 0 || (count > 0 && (!z || !ym || !rho))) return fail(h, SIM_ERR_INVALID_ARG, "bad points");
+        const int m = h->opt.m;
+        RitzInput in;
+        in.arena = &h->arena;
+        in.st = h->st;
+        in.m = m;
+        in.num_slots = h->cap;
+        in.d_H = h->d_H;
+        in.d_meff = h->d_meff;
+        in.d_sigma = h->d_sigma;
+        in.d_beta = h->d_beta;
+        EigDecomposition dec;
+        if (!eig_decompose(in, {s}, dec))
+            return fail(h, SIM_ERR_NOT_CONVERGED, "eigendecomposition of the Hessenberg matrix failed");
+        int me = 0;
+        double beta = 0.0;
+        SIM_CUDA(cudaMemcpyAsync(&me, h->d_meff + s, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        SIM_CUDA(cudaMemcpyAsync(&beta, h->d_beta + s, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        SIM_CUDA(cudaStreamSynchronize(h->st));
+        double2 hl;
+        SIM_CUDA(cudaMemcpy(&hl, h->d_H + (size_t)s * (m + 1) * m + (size_t)(me - 1) * (m + 1) + me, sizeof(double2),
+                            cudaMemcpyDeviceToHost));
+        if (count == 0) return SIM_OK;
+        double2* dz = h->arena.get<double2>("scr_z", count);
+        double2* dy = h->arena.get<double2>("scr_y", count);
+        double* dr = h->arena.get<double>("scr_r", count);
+        SIM_CUDA(cudaMemcpyAsync(dz, z, sizeof(double2) * count, cudaMemcpyHostToDevice, h->st));
+        screen_points(me, std::hypot(hl.x, hl.y), beta, h->h_sigma[s], dec.d, dec.w, dz, count, dy, dr, h->st);
+        SIM_CUDA(cudaMemcpyAsync(ym, dy, sizeof(double2) * count, cudaMemcpyDeviceToHost, h->st));
+        SIM_CUDA(cudaMemcpyAsync(rho, dr, sizeof(double) * count, cudaMemcpyDeviceToHost, h->st));
+        SIM_CUDA(cudaStreamSynchronize(h->st));
         return SIM_OK;
     });
 }

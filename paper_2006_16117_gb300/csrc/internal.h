@@ -96,7 +96,7 @@ __host__ __device__ inline int vs_count(int k) { return VS_Q0 + 2 * k + 1; }
 enum { SC_RNORM0 = 0, SC_RES = 1, SC_GAMMA = 2, SC_WORST = 3, SC_N = 8 };
 enum { IS_STEPS = 0, IS_ITERS = 1, IS_DONE = 2, IS_CYCLE_DONE = 3, IS_BROKEN = 4, IS_STALL = 5, IS_LOOSE = 6, IS_N = 8 };
 
-constexpr int GS_CHUNK = 1024;   // rows per CTA in the Gram–Schmidt kernels
+constexpr int GS_CHUNK = 4096;   // rows per CTA in the Gram–Schmidt kernels (16 per thread)
 constexpr int GS_THREADS = 256;
 
 // ---- krylov.cu ------------------------------------------------------------

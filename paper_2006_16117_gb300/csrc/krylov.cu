@@ -223,48 +223,78 @@ void factor_shifts(const Pencil& P, int precision, const int* d_shift_list, int 
 // ---------------------------------------------------------------------------
 // sparse applies
 // ---------------------------------------------------------------------------
-// y = (A - σB) x  (mode 0)   or   y = rhs - (A - σB) x  (mode 1, rhs in slot r_slot)
-__global__ void k_spmv_jobs(Pencil P, JobSpace js, int x_slot, int y_slot, int rhs_slot, const double2* sigma) {
-    const int job = js.d_active[blockIdx.y];
-    const double2 sg = sigma[js.d_jobshift[job]];
-    const double2* x = js.vec + (size_t)job * js.vstride + (size_t)x_slot * js.n;
-    double2* y = js.vec + (size_t)job * js.vstride + (size_t)y_slot * js.n;
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// y = (A - σB) x, or y = rhs - (A - σB) x when rhs_slot >= 0, for SPMV_RJ
+// active jobs per thread: a thread owns one row and reads its indices and
+// values once for all of its jobs (the jobs' shifts differ only on B's
+// entries), then gathers each job's x.
+constexpr int SPMV_RJ = 4;
+
+__global__ void __launch_bounds__(256) k_spmv_jobs(Pencil P, JobSpace js, int x_slot, int y_slot, int rhs_slot,
+                                                   const double2* sigma, int nactive) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int jb = blockIdx.y * SPMV_RJ;
     if (g >= P.n) return;
-    double2 acc = make_double2(0.0, 0.0);
+    const int nj = min(SPMV_RJ, nactive - jb);
+    const double2* x[SPMV_RJ];
+    double2 sg[SPMV_RJ], acc[SPMV_RJ];
+#pragma unroll
+    for (int r = 0; r < SPMV_RJ; ++r) {
+        const int job = js.d_active[jb + (r < nj ? r : 0)];
+        sg[r] = sigma[js.d_jobshift[job]];
+        x[r] = js.vec + (size_t)job * js.vstride + (size_t)x_slot * js.n;
+        acc[r] = make_double2(0.0, 0.0);
+    }
+    const int64_t e0 = P.rp[g], e1 = P.rp[g + 1];
     if (P.b_kind <= 1) {
-        // B = I or diagonal: A - σB differs from A on the diagonal only, so σB_gg
-        // is formed once and subtracted there (the same value shifted_val gives),
-        // by a select rather than a branch so the loads stay in flight
+        // B = I or diagonal: A - σB differs from A on the diagonal only, where
+        // σB_gg is subtracted (a select rather than a branch keeps the loads in flight)
         const double2 b = P.Bdiag[g];
-        const double sbx = sg.x * b.x - sg.y * b.y, sby = sg.x * b.y + sg.y * b.x;
-        const int64_t e0 = P.rp[g], e1 = P.rp[g + 1];
-#pragma unroll 4
+        double2 sb[SPMV_RJ];
+#pragma unroll
+        for (int r = 0; r < SPMV_RJ; ++r) sb[r] = cmul(sg[r], b);
         for (int64_t e = e0; e < e1; ++e) {
             const int64_t j = P.ci[e];
             const double2 a = P.Ka[e];
             const bool d = j == g;
-            const double2 v = make_double2(d ? a.x - sbx : a.x, d ? a.y - sby : a.y);
-            acc = cfma(v, x[j], acc);
+#pragma unroll
+            for (int r = 0; r < SPMV_RJ; ++r) {
+                if (r < nj) {
+                    const double2 v = make_double2(d ? a.x - sb[r].x : a.x, d ? a.y - sb[r].y : a.y);
+                    acc[r] = cfma(v, x[r][j], acc[r]);
+                }
+            }
         }
     } else {
-        for (int64_t e = P.rp[g]; e < P.rp[g + 1]; ++e) acc = cfma(shifted_val(P, e, sg), x[P.ci[e]], acc);
+        for (int64_t e = e0; e < e1; ++e) {
+            const int64_t j = P.ci[e];
+            const double2 a = P.Ka[e], b = P.Kb[e];
+#pragma unroll
+            for (int r = 0; r < SPMV_RJ; ++r) {
+                if (r < nj) acc[r] = cfma(csub(a, cmul(sg[r], b)), x[r][j], acc[r]);
+            }
+        }
     }
-    if (rhs_slot >= 0) {
-        double2 r = js.vec[(size_t)job * js.vstride + (size_t)rhs_slot * js.n + g];
-        acc = csub(r, acc);
+#pragma unroll
+    for (int r = 0; r < SPMV_RJ; ++r) {
+        if (r >= nj) break;
+        const int job = js.d_active[jb + r];
+        double2 v = acc[r];
+        if (rhs_slot >= 0) v = csub(js.vec[(size_t)job * js.vstride + (size_t)rhs_slot * js.n + g], v);
+        js.vec[(size_t)job * js.vstride + (size_t)y_slot * js.n + g] = v;
     }
-    y[g] = acc;
 }
 
 // y = (A - σB)x (or rhs - (A - σB)x) for the active jobs of the inner solver, timed as "spmv":
-// algorithmic bytes per job 20·nnz + 4(n+1) + 32n (+16n with rhs), 8·nnz flops
+// algorithmic bytes: the matrix (20·nnz + 4(n+1)) once per SPMV_RJ jobs, and
+// per job x and y (32n, +16n with rhs); 8·nnz flops per job
 static void launch_spmv(const Pencil& P, const JobSpace& js, int nactive, int x_slot, int y_slot, int rhs_slot,
                         const double2* d_sigma, cudaStream_t st) {
     kprof_begin("spmv", st);
-    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), nactive), 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma);
+    const int gy = cdiv_up(nactive, SPMV_RJ);
+    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), gy), 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma, nactive);
     SIM_LAUNCH_CHECK();
-    kprof_end("spmv", st, nactive * (20.0 * P.nnz + 4.0 * (P.n + 1) + (rhs_slot >= 0 ? 48.0 : 32.0) * P.n),
+    kprof_end("spmv", st,
+              gy * (20.0 * P.nnz + 4.0 * (P.n + 1)) + nactive * (rhs_slot >= 0 ? 48.0 : 32.0) * P.n,
               nactive * 8.0 * P.nnz);
 }
 
@@ -272,7 +302,8 @@ void spmv_shifted_jobs(const Pencil& P, const JobSpace& js, int nactive, const d
                        const double2* d_sigma, cudaStream_t st) {
     if (nactive <= 0) return;
     // untimed: also the path of the no-allocation entry point
-    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), nactive), 256, 0, st>>>(P, js, x_slot, y_slot, -1, d_sigma);
+    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), cdiv_up(nactive, SPMV_RJ)), 256, 0, st>>>(P, js, x_slot, y_slot, -1, d_sigma,
+                                                                                  nactive);
     SIM_LAUNCH_CHECK();
 }
 

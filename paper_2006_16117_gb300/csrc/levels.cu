@@ -104,12 +104,13 @@ __device__ __forceinline__ EvalSmem carve(unsigned char* raw, int m) {
     return sm;
 }
 
-// choose the nearest untried shift to c (ties: lower id); -1 if none.
-__device__ int next_shift(const ShiftTable& st, double2 c, const uint32_t* tried, double* sred, int* sidx) {
+// choose the nearest untried shift in [lo, hi) to c (ties: lower id); -1 if none.
+__device__ int next_shift(const ShiftTable& st, double2 c, const uint32_t* tried, double* sred, int* sidx, int lo,
+                          int hi) {
     double best = INFINITY;
     int bi = -1;
-    for (int s = threadIdx.x; s < st.S; s += blockDim.x) {
-        if (tried[s >> 5] & (1u << (s & 31))) continue;
+    for (int s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+        if (tried[(s - lo) >> 5] & (1u << ((s - lo) & 31))) continue;
         double d = hypot(st.sigma[s].x - c.x, st.sigma[s].y - c.y);
         if (d < best || (d == best && s < bi)) { best = d; bi = s; }
     }
@@ -148,20 +149,32 @@ __global__ void __launch_bounds__(256) k_eval_level(ShiftTable st, LevelArgs a, 
     __shared__ int sidx[8];
     for (int64_t q = blockIdx.x; q < a.count; q += gridDim.x) {
         if (mode == 1 && !a.todo[q]) continue;
-        const double2 c = square_center(a.re_lo, a.im_lo, a.side, a.ix[q], a.iy[q]);
+        // one pencil: the level's origin and side; a batch: those of the
+        // pencil that owns the square's shift, and only its shifts
+        double re_lo = a.re_lo, im_lo = a.im_lo, side = a.side;
+        int lo = 0, hi = st.S;
+        if (st.pencil_of && mode == 0) {
+            const int p = st.pencil_of[a.sid[q]];
+            re_lo = st.p_re_lo[p];
+            im_lo = st.p_im_lo[p];
+            side = st.p_side[p];
+            lo = st.p_sb[p];
+            hi = st.p_se[p];
+        }
+        const double2 c = square_center(re_lo, im_lo, side, a.ix[q], a.iy[q]);
         for (int w = threadIdx.x; w < SIM_MAX_SHIFTS / 32; w += blockDim.x) tried[w] = 0u;
         __syncthreads();
-        int s = (mode == 0) ? a.sid[q] : next_shift(st, c, tried, sred, sidx);
+        int s = (mode == 0) ? a.sid[q] : next_shift(st, c, tried, sred, sidx, lo, hi);
         double ind0 = 0.0, ind = 0.0;
         bool res = false;
         int first = s;
         int used = s;
-        for (int attempt = 0; s >= 0 && attempt < st.S; ++attempt) {
+        for (int attempt = 0; s >= 0 && attempt < hi - lo; ++attempt) {
             double ii, rr;
-            eval_square(st.H + (size_t)s * (st.m + 1) * st.m, st.m, st.meff[s], st.beta[s], st.sigma[s], c, a.side,
+            eval_square(st.H + (size_t)s * (st.m + 1) * st.m, st.m, st.meff[s], st.beta[s], st.sigma[s], c, side,
                         st.scale, sm, ii, rr);
             if (attempt == 0) ind0 = ii;
-            if (threadIdx.x == 0) tried[s >> 5] |= 1u << (s & 31);
+            if (threadIdx.x == 0) tried[(s - lo) >> 5] |= 1u << ((s - lo) & 31);
             __syncthreads();
             if (rr <= st.eps) {
                 res = true;
@@ -169,9 +182,14 @@ __global__ void __launch_bounds__(256) k_eval_level(ShiftTable st, LevelArgs a, 
                 used = s;
                 break;
             }
-            s = next_shift(st, c, tried, sred, sidx);
+            s = next_shift(st, c, tried, sred, sidx, lo, hi);
         }
         if (threadIdx.x == 0) {
+            if (a.retries) {
+                unsigned int tried_n = 0;
+                for (int w = 0; w < SIM_MAX_SHIFTS / 32; ++w) tried_n += __popc(tried[w]);
+                if (tried_n > 1) atomicAdd(a.retries, (unsigned long long)(tried_n - 1));
+            }
             if (!res) {
                 ind = ind0;
                 used = first;

@@ -21,6 +21,15 @@ struct ShiftTable {
     int scale = 0;                  // 0: residual / ||y||, 1: residual / beta
     double eps = 1e-8;
     double delta0 = 0.05;
+    // batches of pencils (sim_batch_*): shift s belongs to pencil pencil_of[s],
+    // whose squares have their own origin and side (this level) and may only
+    // use that pencil's shifts [p_sb[p], p_se[p]).  nullptr for one pencil.
+    const int* pencil_of = nullptr;
+    const double* p_re_lo = nullptr;
+    const double* p_im_lo = nullptr;
+    const double* p_side = nullptr;
+    const int* p_sb = nullptr;
+    const int* p_se = nullptr;
 };
 
 struct LevelArgs {
@@ -31,6 +40,7 @@ struct LevelArgs {
     uint8_t* mark = nullptr;
     uint8_t* flag = nullptr;
     double* ind = nullptr;
+    unsigned long long* retries = nullptr;  // optional: += evaluations beyond the first shift
     int64_t count = 0;
     double re_lo = 0, im_lo = 0, side = 1;
 };

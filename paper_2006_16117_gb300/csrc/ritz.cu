@@ -16,6 +16,7 @@
 // columns.  k_ritz_pick: one thread per cluster.
 #include <cfloat>
 
+#include "hess.cuh"
 #include "internal.h"
 #include "ritz.h"
 
@@ -181,6 +182,141 @@ __global__ void k_ritz_pick(int C, const double2* est, const double* radius, con
     flag[c] = ok ? 1 : 0;
 }
 
+
+// Sec. 3.2, Eq. zjHm: the eigenvectors of H_m for its eigenvalues d_i (k_ritz),
+// by one step of inverse iteration from e_1 — (H_m - d_i I) v = e_1 as
+// (I - H_m/d_i) v = -e_1/d_i, the warp Hessenberg solve — normalised to unit
+// length: the columns of P.  Then c_1 = P^{-1} e_1 (Gaussian elimination with
+// partial pivoting) and, per eigenvalue, w_i = β e_m^T P e_i c_1[i] (so that
+// e_m^T y = Σ_i w_i / (1 + (σ - z) d_i), Eq. rmLc1) and |c_1[i]|.
+// One CTA of 4 warps per shift; P lives in global scratch (m × m per shift).
+constexpr int EIG_WARPS = 4;
+
+__global__ void __launch_bounds__(EIG_WARPS * 32) k_eigdec(const double2* Hall, int m, const int* meff_all,
+                                                           const double* beta_all, const int* list,
+                                                           const double2* ritz, double2* Pg, double2* w_out,
+                                                           double* absc_out, int* status) {
+    const int s = list[blockIdx.x];
+    const int me = meff_all[s];
+    const double2* H = Hall + (size_t)s * (m + 1) * m;
+    extern __shared__ double2 sh[];
+    double2* Hs = sh;                                   // [me][me]
+    const int usz = me * (me + 1) / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2* U = Hs + (size_t)me * me + (size_t)warp * (usz + me);
+    double2* ys = U + usz;
+    double2* P = Pg + (size_t)blockIdx.x * m * m;       // row-major, leading dimension me
+    const double2* d = ritz + (size_t)blockIdx.x * m;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    stage_H(H, m, me, Hs);
+    __syncthreads();
+    for (int i = warp; i < me; i += EIG_WARPS) {
+        const double2 di = d[i];
+        double ylast = 0.0, yn2 = 0.0;
+        bool ok = false;
+        for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+            // the second attempt moves the shift off an exactly singular pivot
+            const double2 dd = attempt == 0 ? di : cscale(di, 1.0 + 1e-13);
+            const double2 alpha = cdiv(make_double2(-1.0, 0.0), dd);
+            warp_hess_solve(Hs, me, alpha, 1.0, U, ys, ylast, yn2);
+            ok = yn2 > 0.0 && isfinite(yn2);
+        }
+        const double inv = ok ? 1.0 / sqrt(yn2) : 0.0;
+        for (int r = lane; r < me; r += 32) P[(size_t)r * me + i] = cscale(ys[r], inv);
+        if (!ok && lane == 0) s_bad = 1;
+        __syncwarp();
+    }
+    __syncthreads();
+    // c_1 = P^{-1} e_1: eliminate on a copy of P (in the per-warp scratch, 2·me·(me+1) >= me² + me entries)
+    double2* M = Hs + (size_t)me * me;
+    double2* rhs = M + (size_t)me * me;
+    for (int e = threadIdx.x; e < me * me; e += blockDim.x) M[e] = P[e];
+    for (int r = threadIdx.x; r < me; r += blockDim.x) rhs[r] = make_double2(r == 0 ? 1.0 : 0.0, 0.0);
+    __shared__ int s_piv;
+    __syncthreads();
+    for (int k = 0; k < me; ++k) {
+        if (threadIdx.x == 0) {
+            int pr = k;
+            double best = -1.0;
+            for (int r = k; r < me; ++r) {
+                const double v = fabs(M[(size_t)r * me + k].x) + fabs(M[(size_t)r * me + k].y);
+                if (v > best) {
+                    best = v;
+                    pr = r;
+                }
+            }
+            if (!(best > 0.0)) s_bad = 1;
+            s_piv = pr;
+        }
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != k) {
+            for (int c = threadIdx.x; c < me; c += blockDim.x) {
+                const double2 t = M[(size_t)k * me + c];
+                M[(size_t)k * me + c] = M[(size_t)pr * me + c];
+                M[(size_t)pr * me + c] = t;
+            }
+            if (threadIdx.x == 0) {
+                const double2 t = rhs[k];
+                rhs[k] = rhs[pr];
+                rhs[pr] = t;
+            }
+        }
+        __syncthreads();
+        const double2 piv = M[(size_t)k * me + k];
+        const bool zero = piv.x == 0.0 && piv.y == 0.0;
+        for (int e = threadIdx.x; e < (me - k - 1) * (me - k); e += blockDim.x) {
+            const int r = k + 1 + e / (me - k), c = k + e % (me - k);
+            const double2 l = zero ? make_double2(0.0, 0.0) : cdiv(M[(size_t)r * me + k], piv);
+            if (c == k) continue;  // column k is consumed by the factor l (read before it is cleared below)
+            M[(size_t)r * me + c] = csub(M[(size_t)r * me + c], cmul(l, M[(size_t)k * me + c]));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int r = k + 1; r < me; ++r) {
+                const double2 l = zero ? make_double2(0.0, 0.0) : cdiv(M[(size_t)r * me + k], piv);
+                rhs[r] = csub(rhs[r], cmul(l, rhs[k]));
+                M[(size_t)r * me + k] = make_double2(0.0, 0.0);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int r = me - 1; r >= 0; --r) {
+            double2 acc = rhs[r];
+            for (int c = r + 1; c < me; ++c) acc = csub(acc, cmul(M[(size_t)r * me + c], rhs[c]));
+            const double2 dg = M[(size_t)r * me + r];
+            rhs[r] = (dg.x == 0.0 && dg.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(acc, dg);
+        }
+        status[blockIdx.x] = s_bad;
+    }
+    __syncthreads();
+    const double beta = beta_all[s];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        if (i < me) {
+            w_out[(size_t)blockIdx.x * m + i] = cscale(cmul(P[(size_t)(me - 1) * me + i], rhs[i]), beta);
+            absc_out[(size_t)blockIdx.x * m + i] = cabs_h(rhs[i]);
+        } else {
+            w_out[(size_t)blockIdx.x * m + i] = make_double2(0.0, 0.0);
+            absc_out[(size_t)blockIdx.x * m + i] = 0.0;
+        }
+    }
+}
+
+// e_m^T y and the β-relative residual of Eq. eq:error at points z (Eq. rmLc1)
+__global__ void k_screen_points(int me, double hlast, double beta, double2 sigma, const double2* d, const double2* w,
+                                const double2* z, int64_t count, double2* ym, double* rho) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const double2 alpha = csub(sigma, z[t]);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < me; ++i)
+        acc = cadd(acc, cdiv(w[i], make_double2(1.0 + (alpha.x * d[i].x - alpha.y * d[i].y),
+                                                alpha.x * d[i].y + alpha.y * d[i].x)));
+    ym[t] = acc;
+    rho[t] = cabs_h(alpha) * hlast * cabs_h(acc) / beta;
+}
+
 }  // namespace
 
 bool ritz_refine(const RitzInput& in, std::vector<double2>& out, std::vector<int>& flags) {
@@ -230,6 +366,46 @@ bool ritz_refine(const RitzInput& in, std::vector<double2>& out, std::vector<int
     for (int v : status)
         if (v) return false;
     return true;
+}
+
+bool eig_decompose(const RitzInput& in, const std::vector<int>& list, EigDecomposition& out) {
+    const int S = (int)list.size();
+    if (S == 0) return true;
+    DeviceArena& ar = *in.arena;
+    cudaStream_t st = in.st;
+    const int m = in.m;
+    int* d_list = ar.get<int>("ed_list", S);
+    int* d_status = ar.get<int>("ed_status", S);
+    double2* d_ritz = ar.get<double2>("ed_ritz", (int64_t)S * m);
+    double2* d_w = ar.get<double2>("ed_w", (int64_t)S * m);
+    double* d_absc = ar.get<double>("ed_absc", (int64_t)S * m);
+    out.d = d_ritz;
+    out.w = d_w;
+    out.absc = d_absc;
+    double2* Pg = ar.get<double2>("ed_P", (int64_t)S * m * m);
+    SIM_CUDA(cudaMemcpyAsync(d_list, list.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+    SIM_CUDA(cudaMemsetAsync(d_ritz, 0, sizeof(double2) * S * m, st));
+    k_ritz<<<S, 32, (size_t)m * m * sizeof(double2), st>>>(in.d_H, m, in.d_meff, d_list, d_ritz, d_status);
+    SIM_LAUNCH_CHECK();
+    std::vector<int> status(S), status2(S);
+    SIM_CUDA(cudaMemcpyAsync(status.data(), d_status, sizeof(int) * S, cudaMemcpyDeviceToHost, st));
+    const size_t smem = ((size_t)m * m + (size_t)EIG_WARPS * (m * (m + 1) / 2 + m)) * sizeof(double2);
+    SIM_CUDA(cudaFuncSetAttribute(k_eigdec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_eigdec<<<S, EIG_WARPS * 32, smem, st>>>(in.d_H, m, in.d_meff, in.d_beta, d_list, d_ritz, Pg, d_w, d_absc,
+                                             d_status);
+    SIM_LAUNCH_CHECK();
+    SIM_CUDA(cudaMemcpyAsync(status2.data(), d_status, sizeof(int) * S, cudaMemcpyDeviceToHost, st));
+    SIM_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < S; ++i)
+        if (status[i] || status2[i]) return false;
+    return true;
+}
+
+void screen_points(int me, double hlast, double beta, double2 sigma, const double2* d, const double2* w,
+                   const double2* z, int64_t count, double2* ym, double* rho, cudaStream_t st) {
+    if (count <= 0) return;
+    k_screen_points<<<cdiv_up(count, 128), 128, 0, st>>>(me, hlast, beta, sigma, d, w, z, count, ym, rho);
+    SIM_LAUNCH_CHECK();
 }
 
 }  // namespace sim

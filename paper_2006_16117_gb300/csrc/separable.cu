@@ -1,11 +1,11 @@
 // Fast-diagonalisation preconditioner (see separable.h for the formulas).
 //
 // One apply, for every active job at once:
-//   1. w = D^{-1} q            (⊗ρ_d^{-j} scaling, complex128 -> working precision)
+//   1. w = D^{-1} q            (⊗ρ_d^{-j} scaling; complex64 in mixed mode)
 //   2. w = (⊗Q_d) w            (one dense mode product per axis)
-//   3. w = w / (Σ_d λ_{d,k_d} - σ b)   (denominators formed in FP64)
+//   3. w = w / (Σ_d λ_{d,k_d} - σ b)   (denominators and quotients in FP64)
 //   4. w = (⊗Q_d) w
-//   5. z = D w                 (working precision -> complex128)
+//   5. z = D w                 (to complex128)
 // A mode product along axis d is a GEMM over the rows r = (p, q) of the
 // vector viewed as [q][j][p] with p < P = Π_{e<d} N_e and j < N_d:
 //   out(p, k, q) = Σ_j Q_d[k][j] in(p, j, q)      (Q_d symmetric).
@@ -90,16 +90,16 @@ __global__ void k_sep_in(JobSpace js, int in_slot, CW* W, Axes irho) {
     W[(size_t)z * js.n + g] = from_c128<CW>(cmul(x, axes_product(irho, g)));
 }
 
-template <class CW>
-__global__ void k_sep_div(JobSpace js, CW* W, Axes lam, const double2* sigma, double2 b) {
+// out = in / (Σ_d λ_{d,k_d} - σ b), the denominators and the quotient in FP64
+template <class CI, class CO>
+__global__ void k_sep_div(JobSpace js, const CI* in, CO* out, Axes lam, const double2* sigma, double2 b) {
     const int z = blockIdx.y;
     const int job = js.d_active[z];
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= js.n) return;
     const double2 s = sigma[js.d_jobshift[job]];
     const double2 d = csub(axes_sum(lam, g), cmul(s, b));
-    CW& w = W[(size_t)z * js.n + g];
-    w = from_c128<CW>(cdiv(to_c128(w), d));
+    out[(size_t)z * js.n + g] = from_c128<CO>(cdiv(to_c128(in[(size_t)z * js.n + g]), d));
 }
 
 template <class CW>
@@ -196,37 +196,49 @@ Axes axes_of(const Separable& S, double2* const* tab) {
     return a;
 }
 
+// the mode products along every axis, ping-ponging between two buffers;
+// returns the buffer that holds the result
 template <class R>
+cplx<R>* run_modes(const Separable& S, int64_t n, int na, cplx<R>* cur, cplx<R>* nxt, cudaStream_t st) {
+    int64_t P = 1;
+    for (int d = 0; d < S.ndim; ++d) {
+        const int N = (int)S.dims[d];
+        const int64_t rows = n / N;
+        const R* Q = sizeof(R) == 4 ? reinterpret_cast<const R*>(S.Q32[d]) : reinterpret_cast<const R*>(S.Q64[d]);
+        const dim3 grid(cdiv_up(rows, MP_BR), cdiv_up(N, MP_BK), na);
+        if (P == 1) k_sep_mode<R, true><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
+        else k_sep_mode<R, false><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
+        SIM_LAUNCH_CHECK();
+        std::swap(cur, nxt);
+        P *= N;
+    }
+    return cur;
+}
+
+// forward transform S^{-1} in RF, inverse transform S in RB (the division
+// between them in FP64).  Mixed mode runs both transforms in FP32: an FP64
+// inverse transform was measured to leave the inner iteration counts of the
+// 3-D workload unchanged at six times the cost.
+template <class RF, class RB>
 void apply_t(const Separable& S, const JobSpace& js, int na, int in_slot, int out_slot, const double2* d_sigma,
              DeviceArena& ar, cudaStream_t st) {
-    using CW = cplx<R>;
+    using CF = cplx<RF>;
+    using CB = cplx<RB>;
     const int64_t n = js.n;
-    CW* W0 = ar.get<CW>(sizeof(R) == 4 ? "sep_w0_f" : "sep_w0_d", (int64_t)na * n);
-    CW* W1 = ar.get<CW>(sizeof(R) == 4 ? "sep_w1_f" : "sep_w1_d", (int64_t)na * n);
+    CF* F0 = ar.get<CF>(sizeof(RF) == 4 ? "sep_w0_f" : "sep_w0_d", (int64_t)na * n);
+    CF* F1 = ar.get<CF>(sizeof(RF) == 4 ? "sep_w1_f" : "sep_w1_d", (int64_t)na * n);
+    CB* B0 = ar.get<CB>(sizeof(RB) == 4 ? "sep_w0_f" : "sep_w0_d", (int64_t)na * n);
+    CB* B1 = ar.get<CB>(sizeof(RB) == 4 ? "sep_w1_f" : "sep_w1_d", (int64_t)na * n);
     const dim3 eg(cdiv_up(n, 256), na);
-    k_sep_in<CW><<<eg, 256, 0, st>>>(js, in_slot, W0, axes_of(S, S.irho));
+    k_sep_in<CF><<<eg, 256, 0, st>>>(js, in_slot, F0, axes_of(S, S.irho));
     SIM_LAUNCH_CHECK();
-    CW* cur = W0;
-    CW* nxt = W1;
-    auto modes = [&]() {
-        int64_t P = 1;
-        for (int d = 0; d < S.ndim; ++d) {
-            const int N = (int)S.dims[d];
-            const int64_t rows = n / N;
-            const R* Q = sizeof(R) == 4 ? reinterpret_cast<const R*>(S.Q32[d]) : reinterpret_cast<const R*>(S.Q64[d]);
-            const dim3 grid(cdiv_up(rows, MP_BR), cdiv_up(N, MP_BK), na);
-            if (P == 1) k_sep_mode<R, true><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
-            else k_sep_mode<R, false><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
-            SIM_LAUNCH_CHECK();
-            std::swap(cur, nxt);
-            P *= N;
-        }
-    };
-    modes();
-    k_sep_div<CW><<<eg, 256, 0, st>>>(js, cur, axes_of(S, S.lam), d_sigma, S.b);
+    CF* f = run_modes<RF>(S, n, na, F0, F1, st);
+    CB* bout = (void*)f == (void*)B0 ? B1 : B0;  // same buffers in both passes: do not overwrite the input
+    k_sep_div<CF, CB><<<eg, 256, 0, st>>>(js, f, bout, axes_of(S, S.lam), d_sigma, S.b);
     SIM_LAUNCH_CHECK();
-    modes();
-    k_sep_out<CW><<<eg, 256, 0, st>>>(js, out_slot, cur, axes_of(S, S.rho));
+    CB* other = bout == B0 ? B1 : B0;
+    CB* b = run_modes<RB>(S, n, na, bout, other, st);
+    k_sep_out<CB><<<eg, 256, 0, st>>>(js, out_slot, b, axes_of(S, S.rho));
     SIM_LAUNCH_CHECK();
 }
 
@@ -254,8 +266,8 @@ void separable_apply(const Separable& S, int precision, const JobSpace& js, cons
     if (na <= 0) return;
     // the active list is already on the device (js.d_active) in this order
     kprof_begin("separable", st);
-    if (precision == SIM_FP64) apply_t<double>(S, js, na, in_slot, out_slot, d_sigma, ar, st);
-    else apply_t<float>(S, js, na, in_slot, out_slot, d_sigma, ar, st);
+    if (precision == SIM_FP64) apply_t<double, double>(S, js, na, in_slot, out_slot, d_sigma, ar, st);
+    else apply_t<float, float>(S, js, na, in_slot, out_slot, d_sigma, ar, st);
     double flops = 0.0;
     for (int d = 0; d < S.ndim; ++d) flops += 2.0 * 4.0 * (double)js.n * (double)S.dims[d];  // 2 passes, 2 FMA
     const double cw = precision == SIM_FP64 ? 16.0 : 8.0;

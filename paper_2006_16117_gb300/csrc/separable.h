@@ -42,8 +42,8 @@ struct SepCtx {
 void separable_setup(Separable& S, DeviceArena& ar, cudaStream_t st, const std::string& tag = "sep_");
 
 // z_job = (A_s - σ_job b I)^{-1} q_job for the active jobs (vector slots
-// in_slot -> out_slot), complex64 arithmetic in mixed precision (the
-// denominators in FP64), complex128 otherwise.
+// in_slot -> out_slot): the transforms in complex64 in mixed precision
+// (complex128 otherwise), the division in FP64.
 void separable_apply(const Separable& S, int precision, const JobSpace& js, const std::vector<int>& active,
                      int in_slot, int out_slot, const double2* d_sigma, DeviceArena& ar, cudaStream_t st);
 

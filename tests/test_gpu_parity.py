@@ -476,3 +476,32 @@ def test_pencil_levels_and_clusters_equal_the_oracle_record(pencil_run):
     est = np.array(ref["estimate_re"]) + 1j * np.array(ref["estimate_im"])
     assert eig.size == est.size == ref["clusters"]
     assert np.max(np.abs(eig - est)) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_residual_screen_matches_oracle_on_the_same_krylov_space(simlib, precision):
+    """Sec. 3.2 on the GPU (eigendecomposition of H_m, O(m) per point) against
+    the oracle's formula and its direct Hessenberg solve, both fed the GPU's
+    Krylov space of a normal matrix (well-conditioned eigenvectors)."""
+    from oracle import simm as S
+    from workloads import diag_csr
+
+    rng = np.random.default_rng(12)
+    lam = rng.uniform(0, 10, 80) + 1j * rng.uniform(-1, 1, 80)
+    f = rng.standard_normal(80) + 1j * rng.standard_normal(80)
+    s = simlib.Sim(diag_csr(lam), None, simlib.sim_default_options(precision=precision, h0=1e-3))
+    s.set_region((3.0, 7.0, -0.7, 1.3), f)
+    sigma, H, beta, meff = s.get_shift(0)
+    ks = S.KrylovSpace(sigma, H[: meff + 1, :meff], beta, meff)
+    z = sigma + rng.uniform(-2, 2, 64) + 1j * rng.uniform(-1, 1, 64)
+    ym, rho = s.residual_screen(0, z)
+    ym_o, rho_o = S.screened_last_entry(ks, z)
+    y, rho_d = S.projected_solve(ks, z, "beta")
+    d, P, c1, rm = S.eig_decomposition(ks)
+    scale = beta * np.sum(np.abs(rm * c1 / (1.0 + (sigma - z)[:, None] * d)), axis=-1)
+    assert np.all(np.abs(ym - ym_o) <= 1e-9 * np.abs(ym_o) + 1e-11 * scale)
+    assert np.all(np.abs(ym - y[:, -1]) <= 1e-9 * np.abs(y[:, -1]) + 1e-11 * scale)
+    big = np.abs(ym_o) > 1e-6 * scale
+    assert big.sum() >= 10
+    assert np.max(np.abs(rho[big] - rho_d[big]) / rho_d[big]) <= 1e-8
+    s.close()

@@ -158,7 +158,9 @@ def test_cdr2d_full_size_gradients_match_oracle_record_and_differences(simlib):
     d_ref = np.array(ref["dlam_re"]) + 1j * np.array(ref["dlam_im"])
     assert abs(lam - complex(*ref["lam"])) <= 1e-10 * abs(lam)
     assert _rel(dA[pos], d_ref) <= 1e-7
-    # central differences (h = 1e-6) on the GPU along 32 random directions of
+    s.close()
+    # central differences (h = 1e-6) on the GPU, FP64 solves to 1e-14 so that
+    # the differences' rounding (~tol·Φ/h) stays below 1e-5 of them, along 32 random directions of
     # the reaction coefficients: every diagonal entry at once, with the sign of
     # its gradient and a random size in [0.5, 1.5] (one coefficient alone moves
     # Φ by ~1e-12 relative, the rounding level of the solves)
@@ -168,6 +170,8 @@ def test_cdr2d_full_size_gradients_match_oracle_record_and_differences(simlib):
     vals = A.data.copy()
     h = 1e-6
     rng = np.random.default_rng(11)
+    s = simlib.Sim(A, None, simlib.sim_default_options(precision="fp64", inner_tol=1e-14, inner_max_iter=200))
+    s.set_separable(*w.separable)
     for _ in range(32):
         v = np.sign(gA[diag].real) * rng.uniform(0.5, 1.5, diag.size)
         vp, vm = vals.copy(), vals.copy()

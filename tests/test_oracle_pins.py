@@ -445,3 +445,30 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(S, "indicator_from_y", lambda y, off: real_ind(y, np.abs(off)))
     bad, _ = S.evaluate_squares(ks, np.array([c]), np.array([s]))
     assert abs(bad[0] - ref) > 1e-6 * ref
+
+
+def test_eig_decomposition_screen_equals_direct_solve():
+    """Sec. 3.2: e_m^T y = β r_m Λ c_1 equals the last entry of the direct
+    Hessenberg solve for a diagonalisable, well-conditioned H_m (the Krylov
+    space of a normal matrix), and its β-relative residual equals Eq. eq:error's."""
+    rng = np.random.default_rng(12)
+    lam = rng.uniform(0, 10, 80) + 1j * rng.uniform(-1, 1, 80)
+    A = diag_csr(lam).to_scipy()
+    f = rng.standard_normal(80) + 1j * rng.standard_normal(80)
+    ks = S.cayley_arnoldi(A, sp.identity(80, dtype=complex, format="csr"), 5.0 + 0.3j, f, 50)
+    d, P, c1, rm = S.eig_decomposition(ks)
+    assert np.linalg.cond(P) < 1e6
+    z = 5.0 + 0.3j + rng.uniform(-3, 3, 64) + 1j * rng.uniform(-1, 1, 64)
+    y, rho_direct = S.projected_solve(ks, z, "beta")
+    ym, rho_screen = S.screened_last_entry(ks, z, (d, P, c1, rm))
+    # agreement to rounding of the sum: relative where e_m^T y is not tiny, and
+    # within 1e-12 of the sum of the magnitudes of its terms everywhere
+    alpha = ks.sigma - z
+    scale = ks.beta * np.sum(np.abs(rm * c1 / (1.0 + alpha[:, None] * d)), axis=-1)
+    assert np.all(np.abs(ym - y[:, -1]) <= 1e-9 * np.abs(y[:, -1]) + 1e-12 * scale)
+    big = np.abs(y[:, -1]) > 1e-6 * scale
+    assert big.sum() >= 10
+    assert np.max(np.abs(rho_screen[big] - rho_direct[big]) / rho_direct[big]) <= 1e-9
+    # and the decomposition reproduces H_m
+    m = ks.m_eff
+    assert np.linalg.norm(P @ np.diag(d) @ np.linalg.inv(P) - ks.H[:m, :m]) <= 1e-9 * np.linalg.norm(ks.H[:m, :m])

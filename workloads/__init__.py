@@ -27,4 +27,4 @@ from .pencils import (  # noqa: F401
     dense_to_csr,
     complex_gaussian,
 )
-from .configs import config_small, config_pencil, config_jordan_small, config_cdr2d, config_cdr3d, Workload  # noqa: F401
+from .configs import config_small, config_pencil, config_jordan_small, config_cdr2d, config_cdr3d, config_batch, Workload  # noqa: F401

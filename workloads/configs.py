@@ -215,3 +215,44 @@ def config_cdr3d(N: int = 100, width: float = 140.0, seed: int = 0, at: float = 
         options=dict(m=50, n0=4, delta0=0.05, eps=1e-8, h0=1e-6, init_side=1.0),
         separable=((N, N, N), cdr_axes((N, N, N), beta)),
     )
+
+
+# ---------------------------------------------------------------------------
+# batches of independent convection–diffusion pencils of uneven size
+# ---------------------------------------------------------------------------
+@dataclass
+class BatchWorkload:
+    name: str
+    pencils: list          # Workload per pencil (B = I, separable principal part)
+    expected_count: int    # Σ closed-form eigenvalues inside the regions
+
+
+def config_batch(count: int = 64, seed: int = 3, n_lo: int = 45, n_span: int = 179, eig_lo: int = 20,
+                 eig_hi: int = 300) -> BatchWorkload:
+    """`count` pencils -Δu + β_p·∇u on N_p×N_p grids, N_p = n_lo + floor(n_span U_p),
+    Péclet numbers Pe_p ~ U[0.1, 10] with β_p = Pe_p (1, 0.5)/||(1, 0.5)||, B = I
+    (default_rng(seed)).  Each region is the window of c_p ~ U{eig_lo..eig_hi}
+    consecutive closed-form eigenvalues (clipped to the middle third of the
+    spectrum) with the largest smallest gap, Im [-0.3, 0.7]; f_p from seed p."""
+    rng = np.random.default_rng(seed)
+    Ns = n_lo + np.floor(n_span * rng.uniform(size=count)).astype(int)
+    Pe = rng.uniform(0.1, 10.0, count)
+    cs = rng.integers(eig_lo, eig_hi + 1, count)
+    unit = np.array([1.0, 0.5]) / np.linalg.norm([1.0, 0.5])
+    pencils, total = [], 0
+    for p in range(count):
+        N = int(Ns[p])
+        beta = tuple(float(x) for x in Pe[p] * unit)
+        lam = cd2d_eigenvalues(N, beta)
+        lr = np.sort(lam.real)
+        c = int(min(cs[p], lr.size // 3 - 2))
+        start = max_gap_window(lr, c, lr.size // 3, 2 * lr.size // 3)
+        region = window_region(lr, start, c)
+        A = cdr_csr((N, N), beta)
+        pencils.append(Workload(
+            name="cd2d-%dx%d Pe=%.2f (%d eigenvalues)" % (N, N, Pe[p], c), A=A, B=None, region=region,
+            f=complex_gaussian(A.n, p), options=dict(m=50, n0=4, delta0=0.05, eps=1e-8, h0=1e-6),
+            expected_count=c, separable=((N, N), cdr_axes((N, N), beta))))
+        total += c
+    return BatchWorkload(name="%d convection-diffusion pencils, grids %d^2..%d^2, Pe U[0.1,10]" % (
+        count, int(Ns.min()), int(Ns.max())), pencils=pencils, expected_count=total)
