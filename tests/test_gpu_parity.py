@@ -493,7 +493,9 @@ def test_residual_screen_matches_oracle_on_the_same_krylov_space(simlib, precisi
     s.set_region((3.0, 7.0, -0.7, 1.3), f)
     sigma, H, beta, meff = s.get_shift(0)
     ks = S.KrylovSpace(sigma, H[: meff + 1, :meff], beta, meff)
-    z = sigma + rng.uniform(-2, 2, 64) + 1j * rng.uniform(-1, 1, 64)
+    near = lam[np.argsort(np.abs(lam - sigma))[:24]]
+    z = np.concatenate([sigma + rng.uniform(-2, 2, 40) + 1j * rng.uniform(-1, 1, 40),
+                        near + 0.02 * np.exp(2j * np.pi * rng.uniform(size=24))])
     ym, rho = s.residual_screen(0, z)
     ym_o, rho_o = S.screened_last_entry(ks, z)
     y, rho_d = S.projected_solve(ks, z, "beta")
