@@ -108,6 +108,10 @@ typedef struct {
     int32_t mult_reorth;      /* Gram-Schmidt of the multiplicity step's Arnoldi: 0 (default) one
                                  classical pass, as printed in Sec. 2; 1: applied twice (CGS2), as
                                  for the location spaces */
+    int32_t new_shifts_in_levels; /* 0 (default, as printed): shifts are made only by the rounds of
+                                 step 3; 1: at every level, squares no shift resolves get new Krylov
+                                 spaces at their centres (at least shift_sep·side apart, up to
+                                 max_shift_rounds rounds) and the level is evaluated again */
 } sim_options;
 
 /* Counters of the last set_region .. multiplicity sequence. */

@@ -62,6 +62,8 @@ class Options:
     residual_scale: str = "solution"  # "solution": ρ relative to ||y|| = ||x_m||; "beta": relative to β = ||b||
     max_squares: int = 4_000_000    # a level with more squares than this is an error
     mult_reorth: int = 0            # multiplicity spaces: 0 one Gram-Schmidt pass (as printed), 1 CGS2
+    new_shifts_in_levels: int = 0   # 1: squares no shift resolves get new shifts at their centres (step 3's rounds
+                                    # repeated at each level); 0: shifts only at initialisation, as printed
 
 
 # ---------------------------------------------------------------------------
@@ -381,6 +383,21 @@ class SimM:
             s = self.s1 / 2.0 ** (k - 1)
             c = square_centers(re_lo, im_lo, s, ix, iy)
             ind, res, sid = self.resolve(c, s, sid)
+            if o.new_shifts_in_levels:
+                # step 3's rounds at this level: new Krylov spaces at the centres of
+                # unresolved squares (list order, at least shift_sep·s apart), then
+                # every square of the level evaluated again
+                for _ in range(o.max_shift_rounds):
+                    un = np.nonzero(~res)[0]
+                    if un.size == 0:
+                        break
+                    picked = []
+                    for q in un:
+                        if all(abs(c[q] - c[p]) >= o.shift_sep * s for p in picked):
+                            picked.append(q)
+                    for q in picked:
+                        self.add_shift(c[q], self.f)
+                    ind, res, sid = self.resolve(c, s, sid)
             # resolvable: mark iff Ĩ > δ0; unresolvable: mark and flag (step 5)
             mark = np.where(res, ind > o.delta0, True)
             flag = ~res

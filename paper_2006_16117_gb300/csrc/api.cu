@@ -570,6 +570,37 @@ __global__ void k_fill_int(int* out, int64_t n, int v) {
     if (i < n) out[i] = v;
 }
 
+
+// The batch's shift table from every pencil's current shifts: H, β, m_eff, σ
+// and the pencil id at each pencil's offset b->sb[p] (recomputed here).
+void batch_build_table(sim_batch_ctx* b) {
+    const int P = (int)b->h.size();
+    b->sb.assign(1, 0);
+    for (int p = 0; p < P; ++p) b->sb.push_back(b->sb.back() + b->h[p]->S);
+    const int S = b->sb.back();
+    const int m = b->h[0]->opt.m;
+    double2* H = b->arena.get<double2>("H", (int64_t)S * (m + 1) * m);
+    double* beta = b->arena.get<double>("beta", S);
+    int* meff = b->arena.get<int>("meff", S);
+    double2* sigma = b->arena.get<double2>("sigma", S);
+    int* pen = b->arena.get<int>("pencil_of", S);
+    for (int p = 0; p < P; ++p) {
+        sim_ctx* h = b->h[p];
+        const int o = b->sb[p], Sp = h->S;
+        SIM_CUDA(cudaMemcpyAsync(H + (size_t)o * (m + 1) * m, h->d_H, sizeof(double2) * Sp * (m + 1) * m,
+                                 cudaMemcpyDeviceToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(beta + o, h->d_beta, sizeof(double) * Sp, cudaMemcpyDeviceToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(meff + o, h->d_meff, sizeof(int) * Sp, cudaMemcpyDeviceToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(sigma + o, h->d_sigma, sizeof(double2) * Sp, cudaMemcpyDeviceToDevice, b->st));
+        k_fill_int<<<cdiv_up(Sp, 256), 256, 0, b->st>>>(pen + o, Sp, p);
+        SIM_LAUNCH_CHECK();
+    }
+    std::vector<int> psb(b->sb.begin(), b->sb.end() - 1), pse(b->sb.begin() + 1, b->sb.end());
+    SIM_CUDA(cudaMemcpyAsync(b->arena.get<int>("p_sb", P), psb.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->st));
+    SIM_CUDA(cudaMemcpyAsync(b->arena.get<int>("p_se", P), pse.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->st));
+    SIM_CUDA(cudaStreamSynchronize(b->st));
+}
+
 }  // namespace
 
 // Accessors for sim_apply_shifted_noalloc (noalloc.cu).
@@ -623,6 +654,7 @@ void sim_default_options(sim_options* o) {
     o->inner_max_iter = 64;
     o->mult_inner_tol = 1e-10;
     o->mult_reorth = 0;
+    o->new_shifts_in_levels = 0;
 }
 
 sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream, sim_handle* out) {
@@ -639,7 +671,8 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
             o.mult_kmax < o.mult_k || o.mult_kmax > 64 || o.mult_nodes < 4 || o.mult_nodes > 64 ||
             !(o.inner_tol > 0) || !(o.mult_inner_tol > 0) || o.inner_restart < 1 || o.inner_restart > 32 || o.inner_max_iter < 1 ||
             (o.precision != SIM_FP64 && o.precision != SIM_MIXED) || o.max_squares < 1 ||
-            (o.residual_scale != 0 && o.residual_scale != 1) || (o.mult_reorth != 0 && o.mult_reorth != 1))
+            (o.residual_scale != 0 && o.residual_scale != 1) || (o.mult_reorth != 0 && o.mult_reorth != 1) ||
+            (o.new_shifts_in_levels != 0 && o.new_shifts_in_levels != 1))
             return fail(nullptr, SIM_ERR_INVALID_ARG, "options out of range (m must be <= 52, n0 must be 4)");
         HostCsr a, b;
         std::string why;
@@ -913,20 +946,49 @@ sim_status sim_solve_level(sim_handle h, int64_t* n_marked, int32_t* done) {
         la.im_lo = h->im_lo;
         la.side = side;
         la.retries = h->arena.get<unsigned long long>("retries", 1);
-        SIM_CUDA(cudaMemsetAsync(la.retries, 0, sizeof(unsigned long long), h->st));
-        eval_level(shift_table(h), la, 0, h->st);
-        h->stats.squares_evaluated += N;
         const int nbk = cdiv_up(std::max<int64_t>(N, 1), 1024);
         int64_t* bsum = h->arena.get<int64_t>("bsum", nbk + 1);
         int64_t* tot = h->arena.get<int64_t>("tot", 1);
-        h->stats.unresolvable_last_level = count_marked(flag, N, bsum, tot, h->arena.host_i64(), h->st);
-        {
+        bool level_ok = true;
+        for (int round = 0;; ++round) {
+            SIM_CUDA(cudaMemsetAsync(la.retries, 0, sizeof(unsigned long long), h->st));
+            eval_level(shift_table(h), la, 0, h->st);
+            h->stats.squares_evaluated += N;
+            h->stats.unresolvable_last_level = count_marked(flag, N, bsum, tot, h->arena.host_i64(), h->st);
             unsigned long long rt = 0;
             SIM_CUDA(cudaMemcpyAsync(&rt, la.retries, sizeof(rt), cudaMemcpyDeviceToHost, h->st));
             SIM_CUDA(cudaStreamSynchronize(h->st));
             h->stats.shift_retries += (int64_t)rt;
             h->stats.projected_solves += 8 * (N + (int64_t)rt);
+            if (!h->opt.new_shifts_in_levels || h->stats.unresolvable_last_level == 0 ||
+                round >= h->opt.max_shift_rounds)
+                break;
+            // step 3's rounds at this level: new Krylov spaces at the centres of the
+            // unresolved squares (list order, at least shift_sep·side apart), then the
+            // whole level again (resolved squares give the same result)
+            std::vector<uint8_t> hf(N);
+            std::vector<int64_t> hx(N), hy(N);
+            SIM_CUDA(cudaMemcpyAsync(hf.data(), flag, N, cudaMemcpyDeviceToHost, h->st));
+            SIM_CUDA(cudaMemcpyAsync(hx.data(), ix, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, h->st));
+            SIM_CUDA(cudaMemcpyAsync(hy.data(), iy, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, h->st));
+            SIM_CUDA(cudaStreamSynchronize(h->st));
+            const double sep = h->opt.shift_sep * side;
+            std::vector<double2> cen;
+            for (int64_t q = 0; q < N; ++q) {
+                if (!hf[q]) continue;
+                const double2 c = center_of(h, side, hx[q], hy[q]);
+                bool far = true;
+                for (const double2& d : cen)
+                    if (std::hypot(c.x - d.x, c.y - d.y) < sep) {
+                        far = false;
+                        break;
+                    }
+                if (far) cen.push_back(c);
+            }
+            level_ok = build_shifts(h, cen) && level_ok;
+            sync_stats(h);
         }
+        if (!level_ok) return fail(h, SIM_ERR_NOT_CONVERGED, "an inner shifted solve did not converge");
         const int64_t cnt = count_marked(mark, N, bsum, tot, h->arena.host_i64(), h->st);
         const bool last = (k == h->K);
         if (!last) {
@@ -1503,14 +1565,7 @@ sim_status sim_batch_set_regions(sim_batch b, const double* regions, const doubl
             b->im_lo.push_back(h->im_lo);
             b->s1.push_back(h->s1);
         }
-        const int S = b->sb.back();  // every pencil has at most max_shifts <= SIM_MAX_SHIFTS - 1
-        const int m = b->h[0]->opt.m;
-        // the batch's shift table: every pencil's Krylov data at its offset
-        double2* H = b->arena.get<double2>("H", (int64_t)S * (m + 1) * m);
-        double* beta = b->arena.get<double>("beta", S);
-        int* meff = b->arena.get<int>("meff", S);
-        double2* sigma = b->arena.get<double2>("sigma", S);
-        int* pen = b->arena.get<int>("pencil_of", S);
+        batch_build_table(b);
         int64_t N = 0;
         for (int p = 0; p < P; ++p) N += b->h[p]->nsq;
         int64_t* ix = b->arena.get<int64_t>("L0_ix", N);
@@ -1519,14 +1574,7 @@ sim_status sim_batch_set_regions(sim_batch b, const double* regions, const doubl
         int64_t at = 0;
         for (int p = 0; p < P; ++p) {
             sim_ctx* h = b->h[p];
-            const int o = b->sb[p], Sp = h->S;
-            SIM_CUDA(cudaMemcpyAsync(H + (size_t)o * (m + 1) * m, h->d_H, sizeof(double2) * Sp * (m + 1) * m,
-                                     cudaMemcpyDeviceToDevice, b->st));
-            SIM_CUDA(cudaMemcpyAsync(beta + o, h->d_beta, sizeof(double) * Sp, cudaMemcpyDeviceToDevice, b->st));
-            SIM_CUDA(cudaMemcpyAsync(meff + o, h->d_meff, sizeof(int) * Sp, cudaMemcpyDeviceToDevice, b->st));
-            SIM_CUDA(cudaMemcpyAsync(sigma + o, h->d_sigma, sizeof(double2) * Sp, cudaMemcpyDeviceToDevice, b->st));
-            k_fill_int<<<cdiv_up(Sp, 256), 256, 0, b->st>>>(pen + o, Sp, p);
-            SIM_LAUNCH_CHECK();
+            const int o = b->sb[p];
             const int64_t n0 = h->nsq;
             SIM_CUDA(cudaMemcpyAsync(ix + at, h->arena.get<int64_t>("L0_ix", n0), sizeof(int64_t) * n0,
                                      cudaMemcpyDeviceToDevice, b->st));
@@ -1536,9 +1584,6 @@ sim_status sim_batch_set_regions(sim_batch b, const double* regions, const doubl
             SIM_LAUNCH_CHECK();
             at += n0;
         }
-        std::vector<int> psb(b->sb.begin(), b->sb.end() - 1), pse(b->sb.begin() + 1, b->sb.end());
-        SIM_CUDA(cudaMemcpyAsync(b->arena.get<int>("p_sb", P), psb.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->st));
-        SIM_CUDA(cudaMemcpyAsync(b->arena.get<int>("p_se", P), pse.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->st));
         SIM_CUDA(cudaMemcpyAsync(b->arena.get<double>("p_re_lo", P), b->re_lo.data(), sizeof(double) * P,
                                  cudaMemcpyHostToDevice, b->st));
         SIM_CUDA(cudaMemcpyAsync(b->arena.get<double>("p_im_lo", P), b->im_lo.data(), sizeof(double) * P,
@@ -1596,11 +1641,62 @@ sim_status sim_batch_solve_level(sim_batch b, int64_t* n_marked, int32_t* done) 
         la.flag = flag;
         la.ind = b->arena.get<double>("ind", N);
         la.count = N;
-        eval_level(t, la, 0, b->st);
-        b->squares_evaluated += N;
         const int nbk = cdiv_up(std::max<int64_t>(N, 1), 1024);
         int64_t* bsum = b->arena.get<int64_t>("bsum", nbk + 1);
         int64_t* tot = b->arena.get<int64_t>("tot", 1);
+        for (int round = 0;; ++round) {
+            eval_level(t, la, 0, b->st);
+            b->squares_evaluated += N;
+            if (!h0->opt.new_shifts_in_levels || round >= h0->opt.max_shift_rounds) break;
+            const int64_t un = count_marked(flag, N, bsum, tot, b->arena.host_i64(), b->st);
+            if (un == 0) break;
+            // new Krylov spaces at the centres of each pencil's unresolved squares
+            // (as for one pencil), the batch's table rebuilt, and the squares' shift
+            // ids moved to the pencils' new offsets
+            std::vector<uint8_t> hf(N);
+            std::vector<int64_t> hx(N), hy(N);
+            std::vector<int> hs(N);
+            SIM_CUDA(cudaMemcpyAsync(hf.data(), flag, N, cudaMemcpyDeviceToHost, b->st));
+            SIM_CUDA(cudaMemcpyAsync(hx.data(), ix, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, b->st));
+            SIM_CUDA(cudaMemcpyAsync(hy.data(), iy, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, b->st));
+            SIM_CUDA(cudaMemcpyAsync(hs.data(), sid, sizeof(int) * N, cudaMemcpyDeviceToHost, b->st));
+            SIM_CUDA(cudaStreamSynchronize(b->st));
+            const std::vector<int> old_sb = b->sb;
+            auto pencil_of = [&](int g) {
+                return (int)(std::upper_bound(old_sb.begin(), old_sb.end(), g) - old_sb.begin()) - 1;
+            };
+            std::vector<std::vector<double2>> cen(P);
+            for (int64_t q = 0; q < N; ++q) {
+                if (!hf[q]) continue;
+                const int p = pencil_of(hs[q]);
+                const double2 c = center_of(b->h[p], side[p], hx[q], hy[q]);
+                bool far = true;
+                for (const double2& d : cen[p])
+                    if (std::hypot(c.x - d.x, c.y - d.y) < h0->opt.shift_sep * side[p]) {
+                        far = false;
+                        break;
+                    }
+                if (far) cen[p].push_back(c);
+            }
+            bool ok = true;
+            for (int p = 0; p < P; ++p)
+                if (!cen[p].empty()) ok = build_shifts(b->h[p], cen[p]) && ok;
+            if (!ok) return bfail(b, SIM_ERR_NOT_CONVERGED, "an inner shifted solve did not converge");
+            batch_build_table(b);
+            for (int64_t q = 0; q < N; ++q) {
+                const int p = pencil_of(hs[q]);
+                hs[q] = hs[q] - old_sb[p] + b->sb[p];
+            }
+            SIM_CUDA(cudaMemcpyAsync(sid, hs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, b->st));
+            t.H = b->arena.get<double2>("H", 1);
+            t.beta = b->arena.get<double>("beta", 1);
+            t.meff = b->arena.get<int>("meff", 1);
+            t.sigma = b->arena.get<double2>("sigma", 1);
+            t.pencil_of = b->arena.get<int>("pencil_of", 1);
+            t.p_sb = b->arena.get<int>("p_sb", 1);
+            t.p_se = b->arena.get<int>("p_se", 1);
+            t.S = b->sb.back();
+        }
         const int64_t cnt = count_marked(mark, N, bsum, tot, b->arena.host_i64(), b->st);
         const bool last = k == b->K;
         if (!last) {

@@ -92,3 +92,68 @@ def test_batch_equals_single_pencil_runs(simlib):
             s.close()
     finally:
         bt.close()
+
+
+def _p12_record():
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "batch_p12_record.json")) as fh:
+        return json.load(fh)
+
+
+def test_new_shifts_in_levels_record_matches_closed_form():
+    """Pencil 12 of the 64-pencil workload: with new shifts at the levels the
+    oracle locates exactly the closed-form eigenvalues of its region (the
+    record of tests/golden/make_batch_p12_record.py)."""
+    from workloads import cd2d_eigenvalues
+
+    ref = _p12_record()
+    w = config_batch(64).pencils[ref["pencil"]]
+    N = w.separable[0][0]
+    h = 1.0 / (N + 1)
+    beta = tuple(float(((a[2] - a[0]) * h).real) for a in w.separable[1])
+    lam = np.sort(cd2d_eigenvalues(N, beta).real)
+    lo, hi = w.region[:2]
+    inside = lam[(lam > lo) & (lam < hi)]
+    est = np.sort(np.array(ref["estimate_re"]))
+    assert est.size == inside.size == ref["expected_count"]
+    assert np.max(np.abs(est - inside)) <= 1e-6
+    assert np.max(np.abs(ref["estimate_im"])) <= 1e-6
+    assert ref["num_shifts"] > ref["initial_shifts"] and ref["unresolvable_final"] == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_new_shifts_in_levels_gpu_matches_oracle_record(simlib, precision):
+    """The same pencil on the GPU, alone and in a batch with a smaller pencil:
+    levels, shifts and every estimate equal to the oracle's record."""
+    ref = _p12_record()
+    b = config_batch(64)
+    w = b.pencils[ref["pencil"]]
+    opt = simlib.sim_default_options(precision=precision, new_shifts_in_levels=1, **w.options)
+    s = simlib.Sim(w.A, None, opt)
+    try:
+        s.set_separable(*w.separable)
+        s.set_region(w.region, w.f)
+        marked = s.solve_all_levels()
+        eig = s.eigenvalues()
+        st = s.stats()
+    finally:
+        s.close()
+    assert [ref["level_counts"][0]] + [4 * m for m in marked[:-1]] == ref["level_counts"]
+    assert st["num_shifts"] == ref["num_shifts"]
+    est = np.array(ref["estimate_re"]) + 1j * np.array(ref["estimate_im"])
+    assert eig.size == est.size
+    assert np.max(np.abs(eig - est)) <= 1e-9
+    small = _small_batch().pencils[0]
+    bt = simlib.Batch([small.A, w.A], None, opt)
+    try:
+        bt.set_separable(0, *small.separable)
+        bt.set_separable(1, *w.separable)
+        bt.set_regions([small.region, w.region], [small.f, w.f])
+        bt.solve_all_levels()
+        assert np.array_equal(bt.eigenvalues(1), eig)
+        assert bt.stats(1)["num_shifts"] == ref["num_shifts"]
+    finally:
+        bt.close()
