@@ -351,7 +351,10 @@ def secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64
     def bstep(h):
         h.set_regions(regions, fs)
         h.solve_all_levels()
-        loc = sum(int(h.multiplicity(p).sum()) for p in range(h.count))
+        loc = 0
+        for p in range(h.count):
+            h.eigenvalues(p)
+            loc += int(h.multiplicity(p).sum())
         sol = sum(int(h.stats(p)["inner_solves"]) for p in range(h.count))
         return {"located": loc, "solves": sol}
 

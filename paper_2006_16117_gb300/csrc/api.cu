@@ -270,6 +270,16 @@ void upload_pencil(DeviceArena& ar, cudaStream_t st, Pencil& P, const std::vecto
     std::vector<int32_t> L0col(n);
     for (int64_t g = 0; g < n; ++g) L0col[g] = Lptr[g + 1] > Lptr[g] ? Lcol[Lptr[g]] : -1;
     P.L0col = (const int32_t*)up("L0col", L0col.data(), sizeof(int32_t) * L0col.size());
+    P.anorm = P.bnorm = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double ra = 0.0, rb = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            ra += std::hypot(Ka[e].x, Ka[e].y);
+            rb += std::hypot(Kb[e].x, Kb[e].y);
+        }
+        P.anorm = std::max(P.anorm, ra);
+        P.bnorm = std::max(P.bnorm, rb);
+    }
     SIM_CUDA(cudaStreamSynchronize(st));
 }
 

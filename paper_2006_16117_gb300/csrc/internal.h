@@ -50,6 +50,9 @@ struct Pencil {
     // fast-diagonalisation inverse of the pencil's separable part instead of
     // the block factorisation (nothing is factored per shift)
     SepCtx* sep = nullptr;
+    // ||A||_inf and ||B||_inf (row sums of |entries|): the rounding floor of a
+    // shifted residual is about ε (||A|| + |σ| ||B||) ||x||
+    double anorm = 0.0, bnorm = 0.0;
 };
 
 // Offset (in elements of the factor type) of Lval inside a shift's factor.

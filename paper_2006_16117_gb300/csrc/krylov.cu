@@ -486,6 +486,31 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_update(GSArgs a, int accumula
     }
 }
 
+// partial ||w||^2 of each chunk (w read only), into pout[chunk]
+__global__ void __launch_bounds__(GS_THREADS) k_gs_norm_partial(GSArgs a) {
+    const int job = a.active[blockIdx.y];
+    const int chunk = blockIdx.x;
+    const double2* w = a.w + (size_t)job * a.wstride;
+    __shared__ double red[GS_THREADS / 32];
+    const int64_t r0 = (int64_t)chunk * GS_CHUNK;
+    double acc = 0.0;
+    for (int t = 0; t < GS_PER; ++t) {
+        const int64_t r = r0 + threadIdx.x + t * GS_THREADS;
+        if (r < a.n) {
+            const double2 v = w[r];
+            acc += v.x * v.x + v.y * v.y;
+        }
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < GS_THREADS / 32; ++i) sum += red[i];
+        a.pout[((size_t)job * a.nchunk + chunk) * a.pw] = make_double2(sum, 0.0);
+    }
+}
+
 // reduce norm partials, write the subdiagonal entry and normalise w in place
 // (Arnoldi: breakdown test h_{j+1,j} <= btol * ||H_{1:j+1,1:j+1}||_F).
 __global__ void __launch_bounds__(GS_THREADS) k_gs_finish(GSArgs a) {
@@ -685,14 +710,20 @@ __global__ void k_gm_update_x(JobSpace js) {
     base[(size_t)VS_X * js.n + gi] = x;
 }
 
-// explicit residual norm from partials (buffer pin): done if <= tol * rnorm0
-__global__ void k_gm_check(JobSpace js, int nactive, const double2* pin, int nchunk, int pw, double tol, int max_iter) {
+// explicit residual norm from partials (buffer pin), and ||x|| (buffer pinx):
+// done if <= tol * rnorm0
+__global__ void k_gm_check(JobSpace js, int nactive, const double2* pin, const double2* pinx, int nchunk, int pw,
+                           double tol, int max_iter, const double2* sigma, double anorm, double bnorm) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nactive) return;
     const int job = js.d_active[t];
     const double2* P = pin + (size_t)job * nchunk * pw;
-    double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += P[(size_t)c * pw].x;
+    const double2* PX = pinx + (size_t)job * nchunk * pw;
+    double s = 0.0, sx = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+        s += P[(size_t)c * pw].x;
+        sx += PX[(size_t)c * pw].x;
+    }
     double* sc = js.scal + (size_t)job * SC_N;
     int* is = js.istat + (size_t)job * IS_N;
     const double r = sqrt(s);
@@ -703,14 +734,24 @@ __global__ void k_gm_check(JobSpace js, int nactive, const double2* pin, int nch
         is[IS_DONE] = 1;
         return;
     }
+    // The rounding floor of the explicit residual b - (A - σB)x in FP64: about
+    // ε ||A - σB|| ||x|| / ||b|| (||A - σB|| <= ||A||_inf + |σ| ||B||_inf); near an
+    // eigenvalue ||x|| / ||b|| is large and the floor rises above tol.
+    const double2 sg = sigma[js.d_jobshift[job]];
+    const double floor_rel = sc[SC_RNORM0] > 0
+                                 ? 32.0 * 1.1102230246251565e-16 * (anorm + hypot(sg.x, sg.y) * bnorm) * sqrt(sx) /
+                                       sc[SC_RNORM0]
+                                 : 0.0;
+    const double lim = fmax(tol, floor_rel);
     // A restart cycle that did not halve the residual has stagnated.  Stop early
     // only at the rounding floor: after one such cycle if the residual is already
-    // within 10 tol, else after two in a row.  An early stop (or the iteration
-    // cap) accepts the solve within 100 tol, counted as loose, else fails.
+    // within 10 max(tol, floor), else after two in a row.  An early stop (or the
+    // iteration cap) accepts the solve within 100 max(tol, floor), counted as
+    // loose, else fails.
     const int stall = rel > 0.5 * prev ? is[IS_STALL] + 1 : 0;
     is[IS_STALL] = stall;
-    if (is[IS_ITERS] >= max_iter || (stall >= 1 && rel <= 10.0 * tol) || stall >= 2) {
-        const int ok = rel <= 100.0 * tol;
+    if (is[IS_ITERS] >= max_iter || (stall >= 1 && rel <= 10.0 * lim) || stall >= 2) {
+        const int ok = rel <= 100.0 * lim;
         is[IS_DONE] = ok ? 1 : -1;
         is[IS_LOOSE] = ok;
     }
@@ -861,9 +902,14 @@ bool inner_solve(const Pencil& P, const sim_options& opt, JobSpace& js, const st
             const int nw = GS_THREADS / 32;
             k_gs_update<<<dim3(js.nchunk, ni), GS_THREADS, (size_t)(1 + nw) * sizeof(double2) + 64, st>>>(a, 0, 0);
             SIM_LAUNCH_CHECK();
+            // ||x||^2 partials into the second half, for the rounding floor
+            a.w = js.vec + (size_t)VS_X * js.n;
+            a.pout = js.partial + half;
+            k_gs_norm_partial<<<dim3(js.nchunk, ni), GS_THREADS, 0, st>>>(a);
+            SIM_LAUNCH_CHECK();
         }
-        k_gm_check<<<cdiv_up(ni, 128), 128, 0, st>>>(js, ni, js.partial, js.nchunk, js.pw, opt.inner_tol,
-                                                     opt.inner_max_iter);
+        k_gm_check<<<cdiv_up(ni, 128), 128, 0, st>>>(js, ni, js.partial, js.partial + half, js.nchunk, js.pw,
+                                                     opt.inner_tol, opt.inner_max_iter, d_sigma, P.anorm, P.bnorm);
         SIM_LAUNCH_CHECK();
         read_state(js, st);
         std::vector<int> again;
