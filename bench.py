@@ -226,7 +226,7 @@ def run_reference(args, world, rank):
 KERNELS = ("block_solve", "factor", "gram_schmidt", "eval_level", "spmv", "separable")
 
 
-def kernel_roofline(kstats, peaks, src, fp64_tflops, precision):
+def kernel_roofline(kstats, peaks, src, fp64_tflops, precision, fp32_tflops=None):
     """Roofline of the dominant kernel of an instrumented pass: bytes- or
     flop-bound by the kernel's arithmetic (the FP64 streaming kernels are
     bound by the measured FP64 FMA rate, see the DESIGN roofline table)."""
@@ -236,7 +236,7 @@ def kernel_roofline(kstats, peaks, src, fp64_tflops, precision):
     top = max(ks, key=lambda k: ks[k]["ms"])
     k = ks[top]
     per = {"avg_launch_ms": k["ms"] / max(1, k["launches"]), "launches": k["launches"]}
-    hbm_bound = top in ("block_solve", "factor", "spmv") and precision == "mixed" or top == "separable"
+    hbm_bound = top in ("block_solve", "factor", "spmv") and precision == "mixed"
     if top == "block_solve" and precision == "mixed":
         achieved = k["bytes"] / (k["ms"] / 1000.0) / 1e9
         line = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -248,6 +248,13 @@ def kernel_roofline(kstats, peaks, src, fp64_tflops, precision):
         line = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
                 "bytes_per_launch": k["bytes"] / max(1, k["launches"])}
+    elif top == "separable" and precision == "mixed":
+        # dense mode products in FP32: bound by the FP32 pipe
+        achieved = k["flops"] / (k["ms"] / 1000.0) / 1e12
+        line = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp32_tflops if fp32_tflops else None, "traffic": None,
+                "peak_source": "measured FP32 FMA rate of this GPU (sim_measure_fma_peak)",
+                "flops_per_launch": k["flops"] / max(1, k["launches"])}
     else:
         achieved = k["flops"] / (k["ms"] / 1000.0) / 1e12
         line = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
@@ -312,7 +319,7 @@ def single_step_fn(sim, w, f):
     return step
 
 
-def secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64_tflops):
+def secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64_tflops, fp32_tflops):
     """The other configurations, measured with fewer steps (1 warm-up, 1 timed;
     the workload, not the step count, is what they show)."""
     from workloads.configs import config_batch, config_cdr2d, config_cdr3d
@@ -326,7 +333,7 @@ def secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64
         step = single_step_fn(sim, w, f)
         r = timed_steps(torch, sim, s, step, 1, 1, stream, world, local)
         ks = instrumented_pass(sim, s, step)
-        roof, table = kernel_roofline(ks, peaks, src, fp64_tflops, "mixed")
+        roof, table = kernel_roofline(ks, peaks, src, fp64_tflops, "mixed", fp32_tflops)
         st = r["last"]["stats"]
         out[name] = {"workload": w.name, "region": list(w.region), "value": r["located"] / (r["ms_total"] / 1000.0),
                      "unit": "eigenvalues/s", "ms_per_step": r["ms_total"], "warmup": 1, "steps": 1,
@@ -439,7 +446,7 @@ def run_ours(args, world, rank, local):
 
     secondary = None
     if not args.no_secondary and world == 1:
-        secondary = secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64_tflops)
+        secondary = secondary_workloads(args, torch, sim, stream, world, local, peaks, src, fp64_tflops, fp32_tflops)
 
     if rank != 0:
         return
@@ -492,7 +499,7 @@ def run_ours(args, world, rank, local):
         if fe.size == me.size:
             line["quality"]["max_abs_diff_mixed_vs_fp64"] = float(np.max(np.abs(fe - me)))
     # roofline of the dominant kernel, from the instrumented pass (live CUDA events)
-    roof, table = kernel_roofline(mixed["kernels"], peaks, src, fp64_tflops, "mixed")
+    roof, table = kernel_roofline(mixed["kernels"], peaks, src, fp64_tflops, "mixed", fp32_tflops)
     line["roofline"] = roof
     line["kernels"] = table
     line["kernels_total_ms"] = sum(v["ms"] for v in table.values())

@@ -25,6 +25,7 @@
 #include "internal.h"
 #include "levels.h"
 #include "gs.h"
+#include "autotune.h"
 #include "separable.h"
 #include "solve_cluster.h"
 
@@ -226,9 +227,10 @@ void factor_shifts(const Pencil& P, int precision, const int* d_shift_list, int 
 // y = (A - σB) x, or y = rhs - (A - σB) x when rhs_slot >= 0, for SPMV_RJ
 // active jobs per thread: a thread owns one row and reads its indices and
 // values once for all of its jobs (the jobs' shifts differ only on B's
-// entries), then gathers each job's x.
-constexpr int SPMV_RJ = 4;
-
+// entries), then gathers each job's x.  Every job's row sum runs over the
+// row's entries in order, so the result does not depend on SPMV_RJ, which the
+// autotuner picks per matrix (1, 2, 4 or 8).
+template <int SPMV_RJ>
 __global__ void __launch_bounds__(256) k_spmv_jobs(Pencil P, JobSpace js, int x_slot, int y_slot, int rhs_slot,
                                                    const double2* sigma, int nactive) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -284,17 +286,34 @@ __global__ void __launch_bounds__(256) k_spmv_jobs(Pencil P, JobSpace js, int x_
     }
 }
 
+static void spmv_launch_rj(int rj, const Pencil& P, const JobSpace& js, int nactive, int x_slot, int y_slot,
+                           int rhs_slot, const double2* d_sigma, cudaStream_t st) {
+    const dim3 grid(cdiv_up(P.n, 256), cdiv_up(nactive, rj));
+    switch (rj) {
+        case 1: k_spmv_jobs<1><<<grid, 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma, nactive); break;
+        case 2: k_spmv_jobs<2><<<grid, 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma, nactive); break;
+        case 8: k_spmv_jobs<8><<<grid, 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma, nactive); break;
+        default: k_spmv_jobs<4><<<grid, 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma, nactive); break;
+    }
+    SIM_LAUNCH_CHECK();
+}
+
 // y = (A - σB)x (or rhs - (A - σB)x) for the active jobs of the inner solver, timed as "spmv":
-// algorithmic bytes: the matrix (20·nnz + 4(n+1)) once per SPMV_RJ jobs, and
-// per job x and y (32n, +16n with rhs); 8·nnz flops per job
+// algorithmic bytes: the matrix (20·nnz + 4(n+1)) once per RJ jobs, and per
+// job x and y (32n, +16n with rhs); 8·nnz flops per job.  Jobs per thread
+// (RJ) autotuned per matrix and batch size class.
 static void launch_spmv(const Pencil& P, const JobSpace& js, int nactive, int x_slot, int y_slot, int rhs_slot,
                         const double2* d_sigma, cudaStream_t st) {
+    static const int rjs[4] = {1, 2, 4, 8};
+    const int cls = nactive < 4 ? nactive : (nactive < 16 ? 4 : 16);
+    const std::string key = "spmv:" + std::to_string(P.n) + ":" + std::to_string(P.nnz) + ":" + std::to_string(cls);
+    bool timing = false;
+    const int rj = nactive == 1 ? 1 : rjs[autotune_begin(key, 4, st, &timing)];
     kprof_begin("spmv", st);
-    const int gy = cdiv_up(nactive, SPMV_RJ);
-    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), gy), 256, 0, st>>>(P, js, x_slot, y_slot, rhs_slot, d_sigma, nactive);
-    SIM_LAUNCH_CHECK();
+    spmv_launch_rj(rj, P, js, nactive, x_slot, y_slot, rhs_slot, d_sigma, st);
+    if (timing) autotune_end(key, st);
     kprof_end("spmv", st,
-              gy * (20.0 * P.nnz + 4.0 * (P.n + 1)) + nactive * (rhs_slot >= 0 ? 48.0 : 32.0) * P.n,
+              cdiv_up(nactive, rj) * (20.0 * P.nnz + 4.0 * (P.n + 1)) + nactive * (rhs_slot >= 0 ? 48.0 : 32.0) * P.n,
               nactive * 8.0 * P.nnz);
 }
 
@@ -302,9 +321,7 @@ void spmv_shifted_jobs(const Pencil& P, const JobSpace& js, int nactive, const d
                        const double2* d_sigma, cudaStream_t st) {
     if (nactive <= 0) return;
     // untimed: also the path of the no-allocation entry point
-    k_spmv_jobs<<<dim3(cdiv_up(P.n, 256), cdiv_up(nactive, SPMV_RJ)), 256, 0, st>>>(P, js, x_slot, y_slot, -1, d_sigma,
-                                                                                  nactive);
-    SIM_LAUNCH_CHECK();
+    spmv_launch_rj(4, P, js, nactive, x_slot, y_slot, -1, d_sigma, st);
 }
 
 __global__ void k_apply_B(Pencil P, const double2* x, double2* y) {
