@@ -9,13 +9,15 @@
 // A mode product along axis d is a GEMM over the rows r = (p, q) of the
 // vector viewed as [q][j][p] with p < P = Π_{e<d} N_e and j < N_d:
 //   out(p, k, q) = Σ_j Q_d[k][j] in(p, j, q)      (Q_d symmetric).
-// Tiles of 64 rows × 64 outputs, 16 reduction steps per stage, each thread
-// 4 × 4 outputs; loads and stores are coalesced along rows for axes d > 0
-// (consecutive p) and along j / k for axis 0 (contiguous fibres).
+// Tiles of 64 or 128 rows × as many outputs (autotuned), 16 reduction steps
+// per stage, each thread 4 × 4 or 8 × 8 outputs; loads and stores are
+// coalesced along rows for axes d > 0 (consecutive p) and along j / k for
+// axis 0 (contiguous fibres).
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "autotune.h"
 #include "levels.h"
 #include "separable.h"
 
@@ -112,15 +114,20 @@ __global__ void k_sep_out(JobSpace js, int out_slot, const CW* W, Axes rho) {
         cmul(to_c128(W[(size_t)z * js.n + g]), axes_product(rho, g));
 }
 
-constexpr int MP_BR = 64, MP_BK = 64, MP_BJ = 16, MP_THREADS = 256;
+constexpr int MP_BJ = 16, MP_THREADS = 256;
 
 // Y = mode product of X along an axis of length N with inner stride P
 // (rows r = p + P q, element (r, j) at p + P(j + N q)); Q symmetric N×N.
-template <class R, bool AXIS0>
+// Tile TB rows × TB outputs (TB = 64: 4×4 per thread; TB = 128, complex64
+// only: 8×8 per thread, fewer shared-memory loads per multiply-add).  Every output sums its
+// j in the same order in both shapes, so they give bit-identical results and
+// the autotuner picks between them.
+template <class R, bool AXIS0, int TB>
 __global__ void __launch_bounds__(MP_THREADS) k_sep_mode(const cplx<R>* __restrict__ Xall, cplx<R>* __restrict__ Yall,
                                                          const R* __restrict__ Q, int N, int64_t P, int64_t rows,
                                                          int64_t n) {
     using CW = cplx<R>;
+    constexpr int MP_BR = TB, MP_BK = TB, PT = TB / 16;  // PT rows and PT outputs per thread
     __shared__ CW As[MP_BJ][MP_BR + 1];
     __shared__ R Qs[MP_BJ][MP_BK + 1];
     const CW* X = Xall + (size_t)blockIdx.z * n;
@@ -132,14 +139,14 @@ __global__ void __launch_bounds__(MP_THREADS) k_sep_mode(const cplx<R>* __restri
     const int tr = AXIS0 ? t / 16 : t % 16;
     const int tk = AXIS0 ? t % 16 : t / 16;
     const int64_t PN = P * (int64_t)N;
-    CW acc[4][4];
+    CW acc[PT][PT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < PT; ++i)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[i][c] = mk(R(0), R(0));
+        for (int c = 0; c < PT; ++c) acc[i][c] = mk(R(0), R(0));
     for (int j0 = 0; j0 < N; j0 += MP_BJ) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < (MP_BJ * MP_BR) / MP_THREADS; ++i) {
             const int e = t + MP_THREADS * i;
             const int jj = AXIS0 ? e % MP_BJ : e / MP_BR;
             const int rr = AXIS0 ? e / MP_BJ : e % MP_BR;
@@ -155,16 +162,16 @@ __global__ void __launch_bounds__(MP_THREADS) k_sep_mode(const cplx<R>* __restri
         __syncthreads();
 #pragma unroll
         for (int jj = 0; jj < MP_BJ; ++jj) {
-            CW a[4];
-            R q[4];
+            CW a[PT];
+            R q[PT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[jj][tr + 16 * i];
+            for (int i = 0; i < PT; ++i) a[i] = As[jj][tr + 16 * i];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) q[c] = Qs[jj][tk + 16 * c];
+            for (int c = 0; c < PT; ++c) q[c] = Qs[jj][tk + 16 * c];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < PT; ++i)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < PT; ++c) {
                     acc[i][c].x = fma(a[i].x, q[c], acc[i][c].x);
                     acc[i][c].y = fma(a[i].y, q[c], acc[i][c].y);
                 }
@@ -172,12 +179,12 @@ __global__ void __launch_bounds__(MP_THREADS) k_sep_mode(const cplx<R>* __restri
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < PT; ++i) {
         const int64_t r = r0 + tr + 16 * i;
         if (r >= rows) continue;
         const int64_t base = (r % P) + PN * (r / P);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < PT; ++c) {
             const int k = k0 + tk + 16 * c;
             if (k < N) Y[base + P * (int64_t)k] = acc[i][c];
         }
@@ -196,8 +203,17 @@ Axes axes_of(const Separable& S, double2* const* tab) {
     return a;
 }
 
+template <class R, int TB>
+void launch_mode(const cplx<R>* cur, cplx<R>* nxt, const R* Q, int N, int64_t P, int64_t rows, int64_t n, int na,
+                 cudaStream_t st) {
+    const dim3 grid(cdiv_up(rows, TB), cdiv_up(N, TB), na);
+    if (P == 1) k_sep_mode<R, true, TB><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
+    else k_sep_mode<R, false, TB><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
+    SIM_LAUNCH_CHECK();
+}
+
 // the mode products along every axis, ping-ponging between two buffers;
-// returns the buffer that holds the result
+// returns the buffer that holds the result.  Tile shape autotuned per axis.
 template <class R>
 cplx<R>* run_modes(const Separable& S, int64_t n, int na, cplx<R>* cur, cplx<R>* nxt, cudaStream_t st) {
     int64_t P = 1;
@@ -205,10 +221,15 @@ cplx<R>* run_modes(const Separable& S, int64_t n, int na, cplx<R>* cur, cplx<R>*
         const int N = (int)S.dims[d];
         const int64_t rows = n / N;
         const R* Q = sizeof(R) == 4 ? reinterpret_cast<const R*>(S.Q32[d]) : reinterpret_cast<const R*>(S.Q64[d]);
-        const dim3 grid(cdiv_up(rows, MP_BR), cdiv_up(N, MP_BK), na);
-        if (P == 1) k_sep_mode<R, true><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
-        else k_sep_mode<R, false><<<grid, MP_THREADS, 0, st>>>(cur, nxt, Q, N, P, rows, n);
-        SIM_LAUNCH_CHECK();
+        const std::string key = std::string("sep_mode:") + (sizeof(R) == 4 ? "f:" : "d:") + std::to_string(N) + ":" +
+                                std::to_string(P) + ":" + std::to_string(rows) + ":" + std::to_string(na < 4 ? na : 4);
+        bool timing = false;
+        // FP64 keeps the 64-wide tile (8 × 8 complex128 accumulators exceed the register file)
+        const int c = sizeof(R) == 4 ? autotune_begin(key, 2, st, &timing) : 0;
+        if (c == 0) launch_mode<R, 64>(cur, nxt, Q, N, P, rows, n, na, st);
+        else launch_mode<float, 128>(reinterpret_cast<const float2*>(cur), reinterpret_cast<float2*>(nxt),
+                                     reinterpret_cast<const float*>(Q), N, P, rows, n, na, st);
+        if (timing) autotune_end(key, st);
         std::swap(cur, nxt);
         P *= N;
     }
