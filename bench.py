@@ -226,14 +226,14 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-KERNELS = ("block_solve", "factor", "gram_schmidt", "eval_level", "spmv", "separable")
+KERNELS = ("block_solve", "factor", "gram_schmidt", "eval_level", "eval_level_schur", "spmv", "separable")
 
 
 def kernel_roofline(kstats, peaks, src, fp64_tflops, precision, fp32_tflops=None):
     """Roofline of the dominant kernel of an instrumented pass: bytes- or
     flop-bound by the kernel's arithmetic (the FP64 streaming kernels are
     bound by the measured FP64 FMA rate, see the DESIGN roofline table)."""
-    ks = {k: v for k, v in kstats.items() if v}
+    ks = {k: v for k, v in kstats.items() if v and k in KERNELS}
     if not ks:
         return None, {}
     top = max(ks, key=lambda k: ks[k]["ms"])
@@ -300,14 +300,32 @@ def timed_steps(torch, sim, handle, step, warmup, steps, stream, world, local, c
             "last": last, "clocks": ck.stop() if ck else None}
 
 
+# block solve launches by shape: right-hand sides per pass x CTAs per group
+BLOCK_SOLVE_SHAPES = tuple("block_solve_r%d_c%d%s" % (r, c, x) for r in (1, 2, 4, 8) for c in range(1, 17)
+                           for x in ("", "x2"))
+
+
 def instrumented_pass(sim, handle, step):
     """One more step with per-kernel CUDA-event timing (kept out of the timed
     steps: the events add host work per launch)."""
     sim.kernel_timing(True)
     step(handle)
-    ks = {k: sim.kernel_stats(k) for k in KERNELS}
+    ks = {k: sim.kernel_stats(k) for k in KERNELS + BLOCK_SOLVE_SHAPES}
     sim.kernel_timing(False)
     return ks
+
+
+def shape_table(kstats):
+    """The block solve's launches split by shape (a breakdown of its row in
+    the kernel table, not added to the total)."""
+    out = {}
+    for k in BLOCK_SOLVE_SHAPES:
+        v = kstats.get(k)
+        if v and v["launches"]:
+            out[k[len("block_solve_"):]] = {"ms": v["ms"], "launches": v["launches"],
+                                            "GB/s": v["bytes"] / (v["ms"] / 1000.0) / 1e9,
+                                            "GB_per_launch": v["bytes"] / v["launches"] / 1e9}
+    return out
 
 
 def single_step_fn(sim, w, f):
@@ -537,7 +555,9 @@ def run_ours(args, world, rank, local):
                        "max_inner_residual": st["max_inner_residual"],
                        "loose_inner_solves": int(st["loose_inner_solves"]),
                        "gmres_iters_per_solve": st["gmres_iterations"] / max(1, st["inner_solves"]),
-                       "shift_retries": int(st["shift_retries"])}
+                       "shift_retries": int(st["shift_retries"]),
+                       "squares_evaluated": int(st["squares_evaluated"]),
+                       "direct_level_evaluations": int(st["direct_level_evaluations"])}
     if "fp64" in results:
         f = results["fp64"]
         fv = f["located"] / (f["ms_total"] / 1000.0)
@@ -553,6 +573,7 @@ def run_ours(args, world, rank, local):
     line["roofline"] = roof
     line["kernels"] = table
     line["kernels_total_ms"] = sum(v["ms"] for v in table.values())
+    line["block_solve_shapes"] = shape_table(mixed["kernels"])
     line["measured_fma_peaks_tflops"] = {"fp64": fp64_tflops, "fp32": fp32_tflops}
     if secondary is not None:
         line["secondary"] = secondary

@@ -112,6 +112,11 @@ typedef struct {
                                  step 3; 1: at every level, squares no shift resolves get new Krylov
                                  spaces at their centres (at least shift_sep·side apart, up to
                                  max_shift_rounds rounds) and the level is evaluated again */
+    int32_t level_solver;     /* projected solves of the levels (Eqs. eq:many, eq:error): 1 (default)
+                                 the complex Schur form H_m = Z T Z^H of each shift (computed once)
+                                 and one triangular solve per node, with the direct solve for the
+                                 squares their own shift leaves unresolved; 0: Gaussian elimination
+                                 with partial pivoting of I + (σ - z) H_m at every node */
 } sim_options;
 
 /* Counters of the last set_region .. multiplicity sequence. */
@@ -134,6 +139,8 @@ typedef struct {
                                             accepted within 100·inner_tol */
     int64_t unresolvable_last_level;     /* squares of the last solved level no shift resolved */
     int64_t shift_retries;               /* evaluations against a second, third, ... shift (summed) */
+    int64_t direct_level_evaluations;    /* squares evaluated by direct solves (all of them with
+                                            level_solver 0; those the Schur path leaves with 1) */
 } sim_stats_t;
 
 /* Fills *opt with the defaults listed above.  opt must not be NULL. */

@@ -38,7 +38,7 @@ class SimOptions(C.Structure):
         ("mult_seed", C.c_uint64), ("residual_scale", C.c_int32), ("max_squares", C.c_int64),
         ("precision", C.c_int32), ("inner_tol", C.c_double), ("inner_restart", C.c_int32),
         ("inner_max_iter", C.c_int32), ("mult_inner_tol", C.c_double), ("mult_reorth", C.c_int32),
-        ("new_shifts_in_levels", C.c_int32),
+        ("new_shifts_in_levels", C.c_int32), ("level_solver", C.c_int32),
     ]
 
 
@@ -52,6 +52,7 @@ class SimStats(C.Structure):
         ("max_inner_residual", C.c_double), ("t_factor_ms", C.c_double), ("t_krylov_ms", C.c_double),
         ("t_levels_ms", C.c_double), ("t_merge_ms", C.c_double), ("t_mult_ms", C.c_double),
         ("loose_inner_solves", C.c_int64), ("unresolvable_last_level", C.c_int64), ("shift_retries", C.c_int64),
+        ("direct_level_evaluations", C.c_int64),
     ]
 
     def as_dict(self):

@@ -56,6 +56,11 @@ struct sim_ctx {
     double2* d_H = nullptr;
     double* d_beta = nullptr;
     int* d_meff = nullptr;
+    // Schur forms of the Hessenberg matrices (schur.cu)
+    double2* d_schT = nullptr;
+    double2* d_schC = nullptr;
+    double2* d_schQ = nullptr;
+    int* d_schOK = nullptr;
     void** d_fptrs = nullptr;
     size_t factor_bytes = 0;
     // input vector
@@ -291,6 +296,11 @@ void ensure_shift_capacity(sim_ctx* h) {
     h->d_H = h->arena.get<double2>("H", (int64_t)cap * (m + 1) * m);
     h->d_beta = h->arena.get<double>("beta", cap);
     h->d_meff = h->arena.get<int>("meff", cap);
+    h->d_schT = h->arena.get<double2>("schT", (int64_t)cap * m * m);
+    h->d_schC = h->arena.get<double2>("schC", (int64_t)cap * m);
+    h->d_schQ = h->arena.get<double2>("schQ", (int64_t)cap * m);
+    h->d_schOK = h->arena.get<int>("schOK", cap);
+    SIM_CUDA(cudaMemsetAsync(h->d_schOK, 0, sizeof(int) * cap, h->st));
     h->d_fptrs = h->arena.get<void*>("fptrs", cap);
     h->factors.assign(cap, nullptr);
     h->h_sigma.assign(cap, make_double2(0, 0));
@@ -369,6 +379,8 @@ bool build_shifts(sim_ctx* h, const std::vector<double2>& sig) {
         ok = arnoldi(h->P, h->opt, js, h->d_sigma, h->d_fptrs, h->st, h->inner) && ok;
         k_store_space<<<J, 256, 0, h->st>>>(js, J, js.d_jobshift, h->d_H, h->d_beta, h->d_meff, h->opt.m);
         SIM_LAUNCH_CHECK();
+        schur_shifts(h->d_H, h->opt.m, h->d_meff, h->d_beta, h->S, J, h->d_schT, h->d_schC, h->d_schQ, h->d_schOK,
+                     h->st);
         SIM_CUDA(cudaStreamSynchronize(h->st));
         h->S += J;
         h->stats.t_krylov_ms += tk.ms();
@@ -387,7 +399,28 @@ ShiftTable shift_table(sim_ctx* h) {
     t.scale = h->opt.residual_scale;
     t.eps = h->opt.eps;
     t.delta0 = h->opt.delta0;
+    t.schT = h->d_schT;
+    t.schC = h->d_schC;
+    t.schQ = h->d_schQ;
+    t.schOK = h->d_schOK;
     return t;
+}
+
+// One evaluation of a level (mode 0): with level_solver 1 the Schur forms
+// evaluate every square against its own shift and the direct evaluation runs
+// only for the squares they leave; with 0 the direct evaluation runs for all.
+// Returns the number of squares evaluated directly.
+int64_t evaluate_level(const ShiftTable& t, LevelArgs la, int level_solver, DeviceArena& ar, int64_t* bsum,
+                       int64_t* tot, cudaStream_t st) {
+    if (level_solver == 1 && t.schT && la.count > 0) {
+        uint8_t* todo = ar.get<uint8_t>("lvl_todo", la.count);
+        eval_level_schur(t, la, todo, st);
+        la.todo = todo;
+        eval_level(t, la, 0, st);
+        return count_marked(todo, la.count, bsum, tot, ar.host_i64(), st);
+    }
+    eval_level(t, la, 0, st);
+    return la.count;
 }
 
 double2 center_of(const sim_ctx* h, double s, int64_t ix, int64_t iy) {
@@ -594,6 +627,10 @@ void batch_build_table(sim_batch_ctx* b) {
     int* meff = b->arena.get<int>("meff", S);
     double2* sigma = b->arena.get<double2>("sigma", S);
     int* pen = b->arena.get<int>("pencil_of", S);
+    double2* sT = b->arena.get<double2>("schT", (int64_t)S * m * m);
+    double2* sC = b->arena.get<double2>("schC", (int64_t)S * m);
+    double2* sQ = b->arena.get<double2>("schQ", (int64_t)S * m);
+    int* sOK = b->arena.get<int>("schOK", S);
     for (int p = 0; p < P; ++p) {
         sim_ctx* h = b->h[p];
         const int o = b->sb[p], Sp = h->S;
@@ -602,6 +639,13 @@ void batch_build_table(sim_batch_ctx* b) {
         SIM_CUDA(cudaMemcpyAsync(beta + o, h->d_beta, sizeof(double) * Sp, cudaMemcpyDeviceToDevice, b->st));
         SIM_CUDA(cudaMemcpyAsync(meff + o, h->d_meff, sizeof(int) * Sp, cudaMemcpyDeviceToDevice, b->st));
         SIM_CUDA(cudaMemcpyAsync(sigma + o, h->d_sigma, sizeof(double2) * Sp, cudaMemcpyDeviceToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(sT + (size_t)o * m * m, h->d_schT, sizeof(double2) * Sp * m * m,
+                                 cudaMemcpyDeviceToDevice, b->st));
+        SIM_CUDA(cudaMemcpyAsync(sC + (size_t)o * m, h->d_schC, sizeof(double2) * Sp * m, cudaMemcpyDeviceToDevice,
+                                 b->st));
+        SIM_CUDA(cudaMemcpyAsync(sQ + (size_t)o * m, h->d_schQ, sizeof(double2) * Sp * m, cudaMemcpyDeviceToDevice,
+                                 b->st));
+        SIM_CUDA(cudaMemcpyAsync(sOK + o, h->d_schOK, sizeof(int) * Sp, cudaMemcpyDeviceToDevice, b->st));
         k_fill_int<<<cdiv_up(Sp, 256), 256, 0, b->st>>>(pen + o, Sp, p);
         SIM_LAUNCH_CHECK();
     }
@@ -665,6 +709,7 @@ void sim_default_options(sim_options* o) {
     o->mult_inner_tol = 1e-10;
     o->mult_reorth = 0;
     o->new_shifts_in_levels = 0;
+    o->level_solver = 1;
 }
 
 sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream, sim_handle* out) {
@@ -682,7 +727,8 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
             !(o.inner_tol > 0) || !(o.mult_inner_tol > 0) || o.inner_restart < 1 || o.inner_restart > 32 || o.inner_max_iter < 1 ||
             (o.precision != SIM_FP64 && o.precision != SIM_MIXED) || o.max_squares < 1 ||
             (o.residual_scale != 0 && o.residual_scale != 1) || (o.mult_reorth != 0 && o.mult_reorth != 1) ||
-            (o.new_shifts_in_levels != 0 && o.new_shifts_in_levels != 1))
+            (o.new_shifts_in_levels != 0 && o.new_shifts_in_levels != 1) ||
+            (o.level_solver != 0 && o.level_solver != 1))
             return fail(nullptr, SIM_ERR_INVALID_ARG, "options out of range (m must be <= 52, n0 must be 4)");
         HostCsr a, b;
         std::string why;
@@ -962,7 +1008,8 @@ sim_status sim_solve_level(sim_handle h, int64_t* n_marked, int32_t* done) {
         bool level_ok = true;
         for (int round = 0;; ++round) {
             SIM_CUDA(cudaMemsetAsync(la.retries, 0, sizeof(unsigned long long), h->st));
-            eval_level(shift_table(h), la, 0, h->st);
+            h->stats.direct_level_evaluations +=
+                evaluate_level(shift_table(h), la, h->opt.level_solver, h->arena, bsum, tot, h->st);
             h->stats.squares_evaluated += N;
             h->stats.unresolvable_last_level = count_marked(flag, N, bsum, tot, h->arena.host_i64(), h->st);
             unsigned long long rt = 0;
@@ -1636,6 +1683,10 @@ sim_status sim_batch_solve_level(sim_batch b, int64_t* n_marked, int32_t* done) 
         t.p_side = d_side;
         t.p_sb = b->arena.get<int>("p_sb", 1);
         t.p_se = b->arena.get<int>("p_se", 1);
+        t.schT = b->arena.get<double2>("schT", 1);
+        t.schC = b->arena.get<double2>("schC", 1);
+        t.schQ = b->arena.get<double2>("schQ", 1);
+        t.schOK = b->arena.get<int>("schOK", 1);
         const std::string a = "L" + std::to_string(b->cur) + "_", c = "L" + std::to_string(1 - b->cur) + "_";
         const int64_t N = b->nsq;
         int64_t* ix = b->arena.get<int64_t>(a + "ix", N);
@@ -1655,7 +1706,7 @@ sim_status sim_batch_solve_level(sim_batch b, int64_t* n_marked, int32_t* done) 
         int64_t* bsum = b->arena.get<int64_t>("bsum", nbk + 1);
         int64_t* tot = b->arena.get<int64_t>("tot", 1);
         for (int round = 0;; ++round) {
-            eval_level(t, la, 0, b->st);
+            evaluate_level(t, la, h0->opt.level_solver, b->arena, bsum, tot, b->st);
             b->squares_evaluated += N;
             if (!h0->opt.new_shifts_in_levels || round >= h0->opt.max_shift_rounds) break;
             const int64_t un = count_marked(flag, N, bsum, tot, b->arena.host_i64(), b->st);
@@ -1705,6 +1756,10 @@ sim_status sim_batch_solve_level(sim_batch b, int64_t* n_marked, int32_t* done) 
             t.pencil_of = b->arena.get<int>("pencil_of", 1);
             t.p_sb = b->arena.get<int>("p_sb", 1);
             t.p_se = b->arena.get<int>("p_se", 1);
+            t.schT = b->arena.get<double2>("schT", 1);
+            t.schC = b->arena.get<double2>("schC", 1);
+            t.schQ = b->arena.get<double2>("schQ", 1);
+            t.schOK = b->arena.get<int>("schOK", 1);
             t.S = b->sb.back();
         }
         const int64_t cnt = count_marked(mark, N, bsum, tot, b->arena.host_i64(), b->st);

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_eval_level(ShiftTable st, LevelArgs a, 
     __shared__ double sred[8];
     __shared__ int sidx[8];
     for (int64_t q = blockIdx.x; q < a.count; q += gridDim.x) {
-        if (mode == 1 && !a.todo[q]) continue;
+        if (a.todo && !a.todo[q]) continue;
         // one pencil: the level's origin and side; a batch: those of the
         // pencil that owns the square's shift, and only its shifts
         double re_lo = a.re_lo, im_lo = a.im_lo, side = a.side;

@@ -30,13 +30,20 @@ struct ShiftTable {
     const double* p_side = nullptr;
     const int* p_sb = nullptr;
     const int* p_se = nullptr;
+    // complex Schur form H_m = Z T Z^H of each shift (schur.cu): T [S][m][m]
+    // row-major upper triangle, c = β Z^H e_1 [S][m], last row of Z [S][m],
+    // and whether the QR iteration converged [S].  nullptr: not available.
+    const double2* schT = nullptr;
+    const double2* schC = nullptr;
+    const double2* schQ = nullptr;
+    const int* schOK = nullptr;
 };
 
 struct LevelArgs {
     const int64_t* ix = nullptr;
     const int64_t* iy = nullptr;
     int* sid = nullptr;
-    const uint8_t* todo = nullptr;  // association mode: squares to test
+    const uint8_t* todo = nullptr;  // squares to evaluate (all if nullptr in level mode)
     uint8_t* mark = nullptr;
     uint8_t* flag = nullptr;
     double* ind = nullptr;
@@ -100,6 +107,14 @@ struct MergeResult {
     double* radius = nullptr;
     int* rank = nullptr;  // output position, -1 if outside R
 };
+
+// Schur forms of shifts s0 .. s0+count-1 (one warp each).
+void schur_shifts(const double2* H, int m, const int* meff, const double* beta, int s0, int count, double2* T,
+                  double2* C, double2* Q, int* ok, cudaStream_t st);
+// Mode-0 evaluation of every square against its own shift through the Schur
+// forms; todo[q] = 1 for the squares left to eval_level (unresolved by their
+// own shift, or a zero pivot / no Schur form), 0 for those written.
+void eval_level_schur(const ShiftTable& st, const LevelArgs& a, uint8_t* todo, cudaStream_t stream);
 
 size_t eval_smem_bytes(int m);
 void eval_level(const ShiftTable& st, const LevelArgs& a, int mode, cudaStream_t stream);

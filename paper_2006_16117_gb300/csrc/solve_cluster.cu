@@ -25,6 +25,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <map>
 #include <vector>
 
 #include "internal.h"
@@ -150,6 +152,9 @@ template <> struct Vec16<double2> {
     __device__ static __forceinline__ double2 get(const double2& v, int) { return v; }
 };
 
+// two CTAs per SM for single right-hand sides in complex64 (see choose_shape)
+constexpr bool kTwoPerSm = true;
+
 constexpr int CL_WARPS = 8;                       // consumer warps: the GEMVs and the vector work
 constexpr int CL_THREADS = (CL_WARPS + 1) * 32;   // + one producer warp that issues the copies
 
@@ -165,10 +170,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ bool failed_flag(const int* f) { return *(const volatile int*)f != 0; }
 
-template <class C, int R>
-__global__ void __launch_bounds__(CL_THREADS, 1) k_block_solve_cl(Pencil P, JobSpace js, int in_slot, int out_slot,
-                                                               void* const* fptrs, const int* grp_jobs, int SR,
-                                                               int NS, int TP, int* err) {
+// MINB: CTAs per SM the launch is built for (2 caps the registers at 112 so
+// that two CTAs of at most ~112 KB of shared memory share an SM)
+template <class C, int R, int MINB>
+__global__ void __launch_bounds__(CL_THREADS, MINB) k_block_solve_cl(Pencil P, JobSpace js, int in_slot,
+                                                                  int out_slot, void* const* fptrs,
+                                                                  const int* grp_jobs, int SR, int NS, int TP,
+                                                                  int* err) {
     cg::cluster_group cl = cg::this_cluster();
     const int Ccl = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
@@ -552,12 +560,13 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_block_solve_cl(Pencil P, JobS
                         const int rr = rs + r;
                         const int64_t g = g0 + rr;
                         if (!fwd) v = csub(tbuf[(size_t)j * T + (rr - r0)], v);
-                        if (g < P.n) s_out[j][g] = to_c128(v);
+                        // send first: the peers wait for these rows, nobody here waits for the store
                         if (!last) {
                             C* loc = vbuf + (size_t)cur * R * T + (size_t)j * T + rr;
                             for (int qq = 0; qq < Ccl; ++qq)
                                 st_async_c(mapa_u32(loc, qq), v, mapa_u32(&vbar[cur], qq));
                         }
+                        if (g < P.n) s_out[j][g] = to_c128(v);
                     }
                 }
             }
@@ -590,9 +599,9 @@ size_t plan_smem(const Plan& p, int T, size_t cs) {
            (2 * p.NS + 3) * sizeof(uint64_t) + 16;
 }
 
-// Largest R (right-hand sides per pass) and stage height SR that fit.
-bool make_plan(int T, size_t cs, int want_R, Plan& p) {
-    const size_t budget = 220 * 1024;
+// Largest R (right-hand sides per pass) and stage height SR that fit in
+// `budget` bytes of shared memory.
+bool make_plan(int T, size_t cs, int want_R, Plan& p, size_t budget = 220 * 1024) {
     const int TP = padded_row(T, cs);
     for (int R : {8, 4, 2, 1}) {
         if (R > want_R && R != 1) continue;
@@ -614,9 +623,9 @@ bool make_plan(int T, size_t cs, int want_R, Plan& p) {
 
 // Stage height for a CTA of Tc rows: each chunk of `rows` rows occupies the
 // lanes as rows x column phases with rows padded to a power of two, so the
-// estimate charges the padded rows' multiply-adds (FP32: 4 warp-instructions
-// a clock per SM, FP64: one per 16 clocks) plus a fixed cost per chunk (its
-// waits, barrier and epilogue, about 2 us).
+// estimate charges the padded rows' multiply-adds (FP32: 4 warp-instructions a clock per SM,
+// FP64: one per 16 clocks) plus a fixed cost per chunk (its waits, barrier and
+// epilogue, about 2 us).
 int choose_rows(int Tc, int SRmax, int T, size_t cs, int R) {
     const int VN = (int)(16 / cs);
     const int Uw = (T / VN + CL_WARPS - 1) / CL_WARPS;
@@ -640,29 +649,119 @@ int choose_rows(int Tc, int SRmax, int T, size_t cs, int R) {
     return best;
 }
 
-template <class C, int R>
-void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, void* const* fptrs, const int* d_grp,
-               int ngroups, int Ccl, const Plan& pl, int* d_err, cudaStream_t st) {
-    auto kern = k_block_solve_cl<C, R>;
+template <class C, int R, int MINB> void set_smem_attr(size_t smem) {
     static size_t attr_set = 0;  // per instantiation
-    if (pl.smem > attr_set) {
-        SIM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-        attr_set = pl.smem;
+    static bool nonportable = false;
+    if (!nonportable) {
+        // clusters of up to 16 CTAs (beyond the portable 8) for launches of few groups
+        // (where that is refused, the occupancy query reports no room for them)
+        if (cudaFuncSetAttribute(k_block_solve_cl<C, R, MINB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+            (void)cudaGetLastError();
+        nonportable = true;
     }
+    if (smem > attr_set) {
+        SIM_CUDA(cudaFuncSetAttribute(k_block_solve_cl<C, R, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        attr_set = smem;
+    }
+}
+
+cudaLaunchConfig_t cluster_config(int ngroups, int Ccl, size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ngroups * Ccl);
     cfg.blockDim = dim3(CL_THREADS);
-    cfg.dynamicSmemBytes = pl.smem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = Ccl;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SIM_CUDA(cudaLaunchKernelEx(&cfg, kern, P, js, in_slot, out_slot, fptrs, d_grp, pl.SR, pl.NS, pl.TP, d_err));
+    return cfg;
+}
+
+// How many clusters of Ccl CTAs with `smem` bytes each the GPU holds at once
+// (the CUDA occupancy query: clusters are placed within a GPC, so this is not
+// simply SMs / Ccl).  Cached per (instantiation, Ccl, smem).
+template <class C, int R, int MINB> int max_active_clusters(int Ccl, size_t smem) {
+    static std::map<std::pair<int, size_t>, int> cache;
+    const auto key = std::make_pair(Ccl, smem);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    set_smem_attr<C, R, MINB>(smem);
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = cluster_config(1, Ccl, smem, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_block_solve_cl<C, R, MINB>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 0;
+    }
+    cache[key] = n;
+    return n;
+}
+
+template <class C, int R, int MINB>
+void launch_cl(const Pencil& P, const JobSpace& js, int in_slot, int out_slot, void* const* fptrs, const int* d_grp,
+               int ngroups, int Ccl, const Plan& pl, int* d_err, cudaStream_t st) {
+    set_smem_attr<C, R, MINB>(pl.smem);
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = cluster_config(ngroups, Ccl, pl.smem, st, attr);
+    SIM_CUDA(cudaLaunchKernelEx(&cfg, k_block_solve_cl<C, R, MINB>, P, js, in_slot, out_slot, fptrs, d_grp, pl.SR,
+                                pl.NS, pl.TP, d_err));
     SIM_LAUNCH_CHECK();
+}
+
+// Launch shape: CTAs per group (cluster size), CTAs per SM, and the plan.
+struct Shape {
+    int Ccl = 1, minb = 1;
+    Plan pl;
+};
+
+// The shape of a launch of ng groups: every group in one wave if the GPU holds
+// that many clusters, and then the largest cluster (the most SMs, the fewest
+// rows per CTA on the chain's critical path); cluster sizes need not be powers
+// of two.  Two CTAs per SM are considered for single right-hand sides in
+// complex64, whose plan then fits in half of an SM's shared memory.
+template <class C, int R>
+Shape choose_shape(const Pencil& P, size_t cs, const Plan& base, int ng) {
+    Shape best;
+    double best_cost = 1e300;
+    const int cmax = std::min(16, P.T);
+    for (int minb = 1; minb <= 2; ++minb) {
+        if (minb == 2 && !(kTwoPerSm && R == 1 && sizeof(C) == 8)) continue;
+        Plan pl = base;
+        if (minb == 2 && !make_plan(P.T, cs, R, pl, 110 * 1024)) continue;
+        for (int c = 1; c <= cmax; ++c) {
+            Plan q = pl;
+            q.SR = choose_rows((P.T + c - 1) / c, pl.SR, P.T, cs, pl.R);
+            q.smem = plan_smem(q, P.T, cs);
+            int maxc = 0;
+            if constexpr (R == 1 && sizeof(C) == 8)
+                maxc = minb == 1 ? max_active_clusters<C, R, 1>(c, q.smem) : max_active_clusters<C, R, 2>(c, q.smem);
+            else
+                maxc = max_active_clusters<C, R, 1>(c, q.smem);
+            if (maxc <= 0) continue;
+            const int waves = (ng + maxc - 1) / maxc;
+            // waves first, then the fewest rows per CTA, then one CTA per SM
+            const double cost = waves * 1e6 + (double)((P.T + c - 1) / c) * 10.0 + minb;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best.Ccl = c;
+                best.minb = minb;
+                best.pl = q;
+            }
+        }
+    }
+    if (best_cost == 1e300) {  // no occupancy answer: one CTA per group
+        best.Ccl = 1;
+        best.minb = 1;
+        best.pl = base;
+        best.pl.SR = choose_rows(P.T, base.SR, P.T, cs, base.R);
+        best.pl.smem = plan_smem(best.pl, P.T, cs);
+    }
+    return best;
 }
 
 int* g_err = nullptr;
@@ -731,31 +830,47 @@ bool block_solve_cluster(const Pencil& P, int precision, const JobSpace& js, con
     int* d_grp = g_grp + (size_t)fb * g_grp_cap;
     SIM_CUDA(cudaMemcpyAsync(d_grp, g_grp_h[fb], sizeof(int) * flat.size(), cudaMemcpyHostToDevice, st));
     SIM_CUDA(cudaEventRecord(g_grp_ev[fb], st));
-    // cluster size: as many CTAs per group as the 152 SMs allow, up to 8
-    int Ccl = 8;
-    while (Ccl > 1 && (int64_t)Ccl * ng > 152) Ccl >>= 1;
-    Ccl = std::min(Ccl, P.T);
-    pl.SR = choose_rows((P.T + Ccl - 1) / Ccl, pl.SR, P.T, cs, pl.R);
-    pl.smem = plan_smem(pl, P.T, cs);
-    const double TT = (double)P.T * P.T, blocks = 2.0 * P.nb - 1.0;
-    kprof_begin("block_solve", st);
-#define SIM_LAUNCH_R(CT, RR) \
-    launch_cl<CT, RR>(P, js, in_slot, out_slot, d_factor_ptrs, d_grp, ng, Ccl, pl, g_err, st)
+    Shape sh;
     if (precision == SIM_FP64) {
-        if (pl.R == 8) SIM_LAUNCH_R(double2, 8);
-        else if (pl.R == 4) SIM_LAUNCH_R(double2, 4);
-        else if (pl.R == 2) SIM_LAUNCH_R(double2, 2);
-        else SIM_LAUNCH_R(double2, 1);
+        if (pl.R == 8) sh = choose_shape<double2, 8>(P, cs, pl, ng);
+        else if (pl.R == 4) sh = choose_shape<double2, 4>(P, cs, pl, ng);
+        else if (pl.R == 2) sh = choose_shape<double2, 2>(P, cs, pl, ng);
+        else sh = choose_shape<double2, 1>(P, cs, pl, ng);
     } else {
-        if (pl.R == 8) SIM_LAUNCH_R(float2, 8);
-        else if (pl.R == 4) SIM_LAUNCH_R(float2, 4);
-        else if (pl.R == 2) SIM_LAUNCH_R(float2, 2);
-        else SIM_LAUNCH_R(float2, 1);
+        if (pl.R == 8) sh = choose_shape<float2, 8>(P, cs, pl, ng);
+        else if (pl.R == 4) sh = choose_shape<float2, 4>(P, cs, pl, ng);
+        else if (pl.R == 2) sh = choose_shape<float2, 2>(P, cs, pl, ng);
+        else sh = choose_shape<float2, 1>(P, cs, pl, ng);
+    }
+    const int Ccl = sh.Ccl;
+    pl = sh.pl;
+    const double TT = (double)P.T * P.T, blocks = 2.0 * P.nb - 1.0;
+    // instrumentation also files each launch under its shape (right-hand sides
+    // per pass, CTAs per group), e.g. "block_solve_r8_c2"
+    char shape[40];
+    snprintf(shape, sizeof shape, "block_solve_r%d_c%d%s", pl.R, Ccl, sh.minb == 2 ? "x2" : "");
+    kprof_begin("block_solve", st);
+    kprof_begin(shape, st);
+#define SIM_LAUNCH_R(CT, RR, MB) \
+    launch_cl<CT, RR, MB>(P, js, in_slot, out_slot, d_factor_ptrs, d_grp, ng, Ccl, pl, g_err, st)
+    if (precision == SIM_FP64) {
+        if (pl.R == 8) SIM_LAUNCH_R(double2, 8, 1);
+        else if (pl.R == 4) SIM_LAUNCH_R(double2, 4, 1);
+        else if (pl.R == 2) SIM_LAUNCH_R(double2, 2, 1);
+        else SIM_LAUNCH_R(double2, 1, 1);
+    } else {
+        if (pl.R == 8) SIM_LAUNCH_R(float2, 8, 1);
+        else if (pl.R == 4) SIM_LAUNCH_R(float2, 4, 1);
+        else if (pl.R == 2) SIM_LAUNCH_R(float2, 2, 1);
+        else if (sh.minb == 2) SIM_LAUNCH_R(float2, 1, 2);
+        else SIM_LAUNCH_R(float2, 1, 1);
     }
 #undef SIM_LAUNCH_R
     // algorithmic bytes: each group reads the factor once, and 4 vectors per job
-    kprof_end("block_solve", st, ng * blocks * TT * cs + (double)active.size() * 4.0 * P.n * sizeof(double2),
-              (double)active.size() * 8.0 * blocks * TT);
+    const double alg_bytes = ng * blocks * TT * cs + (double)active.size() * 4.0 * P.n * sizeof(double2);
+    const double alg_flops = (double)active.size() * 8.0 * blocks * TT;
+    kprof_end(shape, st, alg_bytes, alg_flops);
+    kprof_end("block_solve", st, alg_bytes, alg_flops);
     return true;
 }
 

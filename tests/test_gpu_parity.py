@@ -206,6 +206,45 @@ def test_simm_jordan_multiplicity(simlib):
     assert np.array_equal(mult, w.reference_mult)
 
 
+@pytest.mark.parametrize("case", ["small", "jordan", "generalized"])
+def test_schur_level_solver_equals_direct_solves(simlib, case):
+    """level_solver 1 (Schur form of H_m per shift, one triangular solve per
+    node, Sec. 3.2) and level_solver 0 (Gaussian elimination of I + (σ - z)H_m
+    at every node) evaluate the same quantities: the same squares are marked at
+    every level and the located eigenvalues are the same square centres.  The
+    Schur path leaves only the squares their own shift does not resolve."""
+    import scipy.linalg as sla
+
+    from workloads import cd2d_csr, config_jordan_small, config_small, diag_csr
+
+    if case == "generalized":
+        A = cd2d_csr(15, (1.0, 0.5))
+        bd = np.random.default_rng(11).uniform(1.0, 2.0, A.n)
+        lr = np.sort(sla.eigvals(A.to_dense(), np.diag(bd)).real)
+        B, region, options = diag_csr(bd), (0.5 * (lr[99] + lr[100]), 0.5 * (lr[119] + lr[120]), -0.3, 0.7), {}
+        f = np.random.default_rng(12).standard_normal(A.n) + 0j
+    else:
+        w = config_small() if case == "small" else config_jordan_small()
+        A, B, region, f, options = w.A, w.B, w.region, w.f, w.options
+    out = []
+    for solver in (0, 1):
+        opt = simlib.sim_default_options(level_solver=solver, **options)
+        s = simlib.Sim(A, B, opt)
+        try:
+            s.set_region(region, f)
+            marked = s.solve_all_levels()
+            out.append((marked, s.eigenvalues(), s.multiplicity(), s.stats()))
+        finally:
+            s.close()
+    (m0, e0, u0, st0), (m1, e1, u1, st1) = out
+    assert m0 == m1
+    assert np.array_equal(e0, e1)
+    assert np.array_equal(u0, u1)
+    assert st0["shift_retries"] == st1["shift_retries"]
+    assert st0["direct_level_evaluations"] == st0["squares_evaluated"]
+    assert st1["direct_level_evaluations"] < st1["squares_evaluated"] // 2
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_multiplicity_single_pass_equals_cgs2(simlib, precision):
     # The multiplicity spaces use one classical Gram-Schmidt pass by default (the

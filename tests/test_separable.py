@@ -190,3 +190,32 @@ def test_simm_cdr2d_full_size_matches_oracle_record(simlib, precision):
     assert eig.size == est.size == w.expected_count
     assert np.max(np.abs(eig - est)) <= 1e-9
     assert np.array_equal(mult, ref["multiplicity"])
+
+
+@pytest.mark.gpu
+def test_cdr3d_full_size_eigenpairs_have_small_residuals(simlib):
+    """n = 10^6 (the 3-D workload at full size, 15-unit sub-region), where no
+    oracle runs: every located eigenvalue, Ritz-refined (Sec. 3.2), with its
+    projection P f (Remark 3.5) is an eigenpair of A to a small backward error
+    ||A x - λ x|| / (|λ| ||x||), and each refined value lies within the
+    precision h0 of its square's estimate."""
+    w = config_cdr3d(100, 15.0)
+    opt = simlib.sim_default_options(precision="mixed", **w.options)
+    s = simlib.Sim(w.A, None, opt)
+    try:
+        s.set_separable(*w.separable)
+        s.set_region(w.region, w.f)
+        s.solve_all_levels()
+        eig = s.eigenvalues()
+        mult = s.multiplicity()
+        ref, flag = s.refine()
+        assert eig.size >= 100 and np.all(mult == 1) and flag.all()
+        assert np.max(np.abs(ref - eig)) <= w.options["h0"]
+        for c in np.random.default_rng(2).choice(eig.size, 6, replace=False):
+            x = torch.from_numpy(s.projection(int(c))).cuda()
+            r = s.apply_shifted(ref[c], x)
+            xn = float(torch.linalg.norm(x))
+            assert xn > 0.0
+            assert float(torch.linalg.norm(r)) <= 1e-8 * abs(ref[c]) * xn, (c, ref[c])
+    finally:
+        s.close()
