@@ -117,6 +117,9 @@ typedef struct {
                                  and one triangular solve per node, with the direct solve for the
                                  squares their own shift leaves unresolved; 0: Gaussian elimination
                                  with partial pivoting of I + (σ - z) H_m at every node */
+    int32_t separable_tensor_cores; /* mixed precision with sim_set_separable: 1 (default) the mode
+                                 products on the tensor cores (tcgen05, TF32 with hi/lo splitting to
+                                 FP32 accuracy); 0: FP32 CUDA-core GEMMs */
 } sim_options;
 
 /* Counters of the last set_region .. multiplicity sequence. */

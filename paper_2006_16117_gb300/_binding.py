@@ -38,7 +38,7 @@ class SimOptions(C.Structure):
         ("mult_seed", C.c_uint64), ("residual_scale", C.c_int32), ("max_squares", C.c_int64),
         ("precision", C.c_int32), ("inner_tol", C.c_double), ("inner_restart", C.c_int32),
         ("inner_max_iter", C.c_int32), ("mult_inner_tol", C.c_double), ("mult_reorth", C.c_int32),
-        ("new_shifts_in_levels", C.c_int32), ("level_solver", C.c_int32),
+        ("new_shifts_in_levels", C.c_int32), ("level_solver", C.c_int32), ("separable_tensor_cores", C.c_int32),
     ]
 
 

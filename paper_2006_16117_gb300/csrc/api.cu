@@ -710,6 +710,7 @@ void sim_default_options(sim_options* o) {
     o->mult_reorth = 0;
     o->new_shifts_in_levels = 0;
     o->level_solver = 1;
+    o->separable_tensor_cores = 1;
 }
 
 sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt, void* stream, sim_handle* out) {
@@ -728,7 +729,8 @@ sim_status sim_create(const sim_csr* A, const sim_csr* B, const sim_options* opt
             (o.precision != SIM_FP64 && o.precision != SIM_MIXED) || o.max_squares < 1 ||
             (o.residual_scale != 0 && o.residual_scale != 1) || (o.mult_reorth != 0 && o.mult_reorth != 1) ||
             (o.new_shifts_in_levels != 0 && o.new_shifts_in_levels != 1) ||
-            (o.level_solver != 0 && o.level_solver != 1))
+            (o.level_solver != 0 && o.level_solver != 1) ||
+            (o.separable_tensor_cores != 0 && o.separable_tensor_cores != 1))
             return fail(nullptr, SIM_ERR_INVALID_ARG, "options out of range (m must be <= 52, n0 must be 4)");
         HostCsr a, b;
         std::string why;
@@ -1354,6 +1356,7 @@ sim_status sim_set_separable(sim_handle h, int32_t ndim, const int64_t* dims, co
             if (dims[d] > 1 && ((sub.x == 0 && sub.y == 0) || (sup.x == 0 && sup.y == 0)))
                 return fail(h, SIM_ERR_INVALID_ARG, "an axis with a zero off-diagonal is not diagonalisable");
         }
+        sep->S.tc = h->opt.separable_tensor_cores != 0;
         sep->ar = &h->arena;
         separable_setup(sep->S, h->arena, h->st);
         // the factorisations of an earlier region are no longer used

@@ -3,7 +3,8 @@
 // One apply, for every active job at once:
 //   1. w = D^{-1} q            (⊗ρ_d^{-j} scaling; complex64 in mixed mode)
 //   2. w = (⊗Q_d) w            (one dense mode product per axis)
-//   3. w = w / (Σ_d λ_{d,k_d} - σ b)   (denominators and quotients in FP64)
+//   3. w = w / (Σ_d λ_{d,k_d} - σ b)   (denominators in FP64; the quotient in
+//      FP32 in mixed mode, from per-element tables of Σ_d λ and of the scales)
 //   4. w = (⊗Q_d) w
 //   5. z = D w                 (to complex128)
 // A mode product along axis d is a GEMM over the rows r = (p, q) of the
@@ -80,6 +81,54 @@ __device__ __forceinline__ double2 axes_sum(const Axes& a, int64_t idx) {
         if (a.ndim > 2) v = cadd(v, a.t2[idx / (a.N0 * a.N1)]);
     }
     return v;
+}
+
+// per-element tables of the complex64 path, formed in FP64 once
+__global__ void k_sep_elem_tables(int64_t n, Axes irho, Axes rho, Axes lam, float2* sin32, float2* sout32,
+                                  double2* lsum) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    sin32[g] = from_c128<float2>(axes_product(irho, g));
+    sout32[g] = from_c128<float2>(axes_product(rho, g));
+    lsum[g] = axes_sum(lam, g);
+}
+
+// complex64 path: w = x D^{-1} with the per-element scale in FP32 (the input
+// rounded to FP32 first: FP64 arithmetic is scarce on this GPU)
+__global__ void k_sep_in32(JobSpace js, int in_slot, float2* W, const float2* __restrict__ sc) {
+    const int z = blockIdx.y;
+    const int job = js.d_active[z];
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= js.n) return;
+    const float2 x = from_c128<float2>(js.vec[(size_t)job * js.vstride + (size_t)in_slot * js.n + g]);
+    const float2 s = sc[g];
+    W[(size_t)z * js.n + g] = make_float2(x.x * s.x - x.y * s.y, x.x * s.y + x.y * s.x);
+}
+
+// complex64 path: out = in / (Σ_d λ - σb), the denominator formed in FP64 from
+// the FP64 sum table and rounded once, the quotient in FP32
+__global__ void k_sep_div32(JobSpace js, const float2* in, float2* out, const double2* __restrict__ lsum,
+                            const double2* sigma, double2 b) {
+    const int z = blockIdx.y;
+    const int job = js.d_active[z];
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= js.n) return;
+    const double2 s = sigma[js.d_jobshift[job]];
+    const float2 d = from_c128<float2>(csub(lsum[g], cmul(s, b)));
+    const float2 v = in[(size_t)z * js.n + g];
+    const float inv = 1.0f / (d.x * d.x + d.y * d.y);
+    out[(size_t)z * js.n + g] = make_float2((v.x * d.x + v.y * d.y) * inv, (v.y * d.x - v.x * d.y) * inv);
+}
+
+// complex64 path: z = D w, the scale in FP32, the result stored in FP64
+__global__ void k_sep_out32(JobSpace js, int out_slot, const float2* W, const float2* __restrict__ sc) {
+    const int z = blockIdx.y;
+    const int job = js.d_active[z];
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= js.n) return;
+    const float2 w = W[(size_t)z * js.n + g], s = sc[g];
+    js.vec[(size_t)job * js.vstride + (size_t)out_slot * js.n + g] =
+        to_c128(make_float2(w.x * s.x - w.y * s.y, w.x * s.y + w.y * s.x));
 }
 
 template <class CW>
@@ -217,10 +266,21 @@ void launch_mode(const cplx<R>* cur, cplx<R>* nxt, const R* Q, int N, int64_t P,
 template <class R>
 cplx<R>* run_modes(const Separable& S, int64_t n, int na, cplx<R>* cur, cplx<R>* nxt, cudaStream_t st) {
     int64_t P = 1;
+    // instrumentation: the mode products alone (a part of "separable")
+    kprof_begin(sizeof(R) == 4 && S.tc ? "sep_mode_tc" : "sep_mode", st);
+    double flops = 0.0;
+    for (int d = 0; d < S.ndim; ++d) flops += 4.0 * (double)n * (double)S.dims[d] * na;
     for (int d = 0; d < S.ndim; ++d) {
         const int N = (int)S.dims[d];
         const int64_t rows = n / N;
         const R* Q = sizeof(R) == 4 ? reinterpret_cast<const R*>(S.Q32[d]) : reinterpret_cast<const R*>(S.Q64[d]);
+        if (sizeof(R) == 4 && S.tc &&
+            sep_mode_tc(reinterpret_cast<const float2*>(cur), reinterpret_cast<float2*>(nxt), S.Qh[d], S.Ql[d], N, P,
+                        rows, n, na, st)) {
+            std::swap(cur, nxt);
+            P *= N;
+            continue;
+        }
         const std::string key = std::string("sep_mode:") + (sizeof(R) == 4 ? "f:" : "d:") + std::to_string(N) + ":" +
                                 std::to_string(P) + ":" + std::to_string(rows) + ":" + std::to_string(na < 4 ? na : 4);
         bool timing = false;
@@ -233,6 +293,8 @@ cplx<R>* run_modes(const Separable& S, int64_t n, int na, cplx<R>* cur, cplx<R>*
         std::swap(cur, nxt);
         P *= N;
     }
+    kprof_end(sizeof(R) == 4 && S.tc ? "sep_mode_tc" : "sep_mode", st, 2.0 * S.ndim * (double)na * n * sizeof(cplx<R>),
+              flops);
     return cur;
 }
 
@@ -251,15 +313,19 @@ void apply_t(const Separable& S, const JobSpace& js, int na, int in_slot, int ou
     CB* B0 = ar.get<CB>(sizeof(RB) == 4 ? "sep_w0_f" : "sep_w0_d", (int64_t)na * n);
     CB* B1 = ar.get<CB>(sizeof(RB) == 4 ? "sep_w1_f" : "sep_w1_d", (int64_t)na * n);
     const dim3 eg(cdiv_up(n, 256), na);
-    k_sep_in<CF><<<eg, 256, 0, st>>>(js, in_slot, F0, axes_of(S, S.irho));
+    constexpr bool c64 = sizeof(RF) == 4 && sizeof(RB) == 4;
+    if constexpr (c64) k_sep_in32<<<eg, 256, 0, st>>>(js, in_slot, F0, S.sin32);
+    else k_sep_in<CF><<<eg, 256, 0, st>>>(js, in_slot, F0, axes_of(S, S.irho));
     SIM_LAUNCH_CHECK();
     CF* f = run_modes<RF>(S, n, na, F0, F1, st);
     CB* bout = (void*)f == (void*)B0 ? B1 : B0;  // same buffers in both passes: do not overwrite the input
-    k_sep_div<CF, CB><<<eg, 256, 0, st>>>(js, f, bout, axes_of(S, S.lam), d_sigma, S.b);
+    if constexpr (c64) k_sep_div32<<<eg, 256, 0, st>>>(js, f, bout, S.lsum, d_sigma, S.b);
+    else k_sep_div<CF, CB><<<eg, 256, 0, st>>>(js, f, bout, axes_of(S, S.lam), d_sigma, S.b);
     SIM_LAUNCH_CHECK();
     CB* other = bout == B0 ? B1 : B0;
     CB* b = run_modes<RB>(S, n, na, bout, other, st);
-    k_sep_out<CB><<<eg, 256, 0, st>>>(js, out_slot, b, axes_of(S, S.rho));
+    if constexpr (c64) k_sep_out32<<<eg, 256, 0, st>>>(js, out_slot, b, S.sout32);
+    else k_sep_out<CB><<<eg, 256, 0, st>>>(js, out_slot, b, axes_of(S, S.rho));
     SIM_LAUNCH_CHECK();
 }
 
@@ -274,10 +340,21 @@ void separable_setup(Separable& S, DeviceArena& ar, cudaStream_t st, const std::
         S.rho[d] = ar.get<double2>(tag + "rho", N);
         S.irho[d] = ar.get<double2>(tag + "irho", N);
         S.lam[d] = ar.get<double2>(tag + "lam", N);
+        S.Qh[d] = ar.get<float>(tag + "Qh", N * N);
+        S.Ql[d] = ar.get<float>(tag + "Ql", N * N);
         k_sep_tables<<<cdiv_up(N * N, 256), 256, 0, st>>>((int)N, S.axis[d][0], S.axis[d][1], S.axis[d][2], S.Q64[d],
                                                          S.Q32[d], S.rho[d], S.irho[d], S.lam[d]);
         SIM_LAUNCH_CHECK();
+        sep_split_tables(S.Q64[d], (int)N, S.Qh[d], S.Ql[d], st);
     }
+    int64_t n = 1;
+    for (int d = 0; d < S.ndim; ++d) n *= S.dims[d];
+    S.sin32 = ar.get<float2>(prefix + "sin32", n);
+    S.sout32 = ar.get<float2>(prefix + "sout32", n);
+    S.lsum = ar.get<double2>(prefix + "lsum", n);
+    k_sep_elem_tables<<<cdiv_up(n, 256), 256, 0, st>>>(n, axes_of(S, S.irho), axes_of(S, S.rho), axes_of(S, S.lam),
+                                                      S.sin32, S.sout32, S.lsum);
+    SIM_LAUNCH_CHECK();
     SIM_CUDA(cudaStreamSynchronize(st));
 }
 

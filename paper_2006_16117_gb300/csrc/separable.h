@@ -31,6 +31,16 @@ struct Separable {
     double2* rho[3] = {nullptr, nullptr, nullptr};
     double2* irho[3] = {nullptr, nullptr, nullptr};
     double2* lam[3] = {nullptr, nullptr, nullptr};
+    // Q split for the tensor cores: Q = Qh + Ql, Qh exact in TF32 (FP32 tables)
+    float* Qh[3] = {nullptr, nullptr, nullptr};
+    float* Ql[3] = {nullptr, nullptr, nullptr};
+    bool tc = false;  // complex64 mode products on the tensor cores (separable_tc.cu)
+    // per element, for the complex64 path: Π_d ρ_d^{-j_d} and Π_d ρ_d^{j_d} rounded
+    // from FP64, and Σ_d λ_{d,k_d} in FP64 (so the denominator's cancellation
+    // against σb still happens in FP64)
+    float2* sin32 = nullptr;
+    float2* sout32 = nullptr;
+    double2* lsum = nullptr;
 };
 
 struct SepCtx {
@@ -40,6 +50,12 @@ struct SepCtx {
 
 // Builds the per-axis tables on the device (arena buffers tag + "ax*").
 void separable_setup(Separable& S, DeviceArena& ar, cudaStream_t st, const std::string& tag = "sep_");
+
+// One mode product of na complex64 vectors on the tensor cores (3xTF32),
+// Y = X ×_axis Q for an axis of length N with inner stride P (separable_tc.cu).
+bool sep_mode_tc(const float2* cur, float2* nxt, const float* Qhi, const float* Qlo, int N, int64_t P, int64_t rows,
+                 int64_t n, int na, cudaStream_t st);
+void sep_split_tables(const double* Q64, int N, float* Qhi, float* Qlo, cudaStream_t st);
 
 // z_job = (A_s - σ_job b I)^{-1} q_job for the active jobs (vector slots
 // in_slot -> out_slot): the transforms in complex64 in mixed precision

@@ -108,6 +108,39 @@ def test_separable_shifted_solve_matches_sparse_lu(simlib, precision, case):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("dims", [(40, 33), (10, 12, 9), (300, 7)])
+def test_separable_tensor_core_mode_products_equal_cuda_cores(simlib, dims):
+    """Mixed precision: the mode products on the tensor cores (TF32 with hi/lo
+    splitting) and on the CUDA cores (FP32) are the same preconditioner to FP32
+    accuracy, so the FP64 FGMRES around them takes the same number of steps
+    (give or take one) to the same solution.  Axis lengths cover one output tile
+    (33, 40), several (300) and lengths that are not multiples of 4 or 16."""
+    from workloads import cdr_axes
+
+    beta = (1.0, 0.5, 0.25)[: len(dims)]
+    rng = np.random.default_rng(5)
+    n = int(np.prod(dims))
+    react = 0.3 * np.sqrt(rng.uniform(size=n)) * np.exp(2j * np.pi * rng.uniform(size=n))
+    A = cdr_csr(dims, beta, react)
+    lam = np.sort(cdr_separable_eigenvalues(dims, beta).real)
+    sigma = lam[len(lam) // 3] + 0.37 + 0.2j
+    r = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n)).cuda()
+    ref = spla.splu((A.to_scipy() - sigma * sp.identity(n)).tocsc()).solve(r.cpu().numpy())
+    out = []
+    for tc in (0, 1):
+        s = simlib.Sim(A, None, simlib.sim_default_options(precision="mixed", separable_tensor_cores=tc))
+        try:
+            s.set_separable(dims, cdr_axes(dims, beta))
+            x, iters, rel = s.shifted_solve(sigma, r)
+        finally:
+            s.close()
+        assert rel <= 1e-12
+        assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
+        out.append(iters)
+    assert abs(out[0] - out[1]) <= 1, out
+
+
+@pytest.mark.gpu
 def test_set_separable_rejects_bad_input(simlib):
     from workloads import cdr_axes, diag_csr
 
