@@ -104,7 +104,8 @@ typedef struct {
     int32_t inner_restart;    /* GMRES restart length (8) */
     int32_t inner_max_iter;   /* GMRES iteration cap per solve (64) */
     double mult_inner_tol;    /* inner tolerance for the multiplicity step's Krylov spaces,
-                                 which feed only a rank test at mult_tol (1e-10) */
+                                 which feed only a rank test at mult_tol (1e-10; 1e-8 was measured
+                                 to count simple eigenvalues of the 2-D reaction workload twice) */
     int32_t mult_reorth;      /* Gram-Schmidt of the multiplicity step's Arnoldi: 0 (default) one
                                  classical pass, as printed in Sec. 2; 1: applied twice (CGS2), as
                                  for the location spaces */
