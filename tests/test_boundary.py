@@ -55,6 +55,21 @@ def test_default_options_and_struct_layout(built):
     assert o.inner_tol == 1e-12 and o.inner_restart == 8
 
 
+def test_option_defaults_and_range_checks_without_a_gpu(built):
+    o = built.sim_default_options()
+    assert o.level_solver == 1 and o.separable_tensor_cores == 1 and o.new_shifts_in_levels == 0
+    assert o.mult_inner_tol == 1e-10 and o.mult_reorth == 0
+    lib = built.lib()
+    h = ctypes.c_void_p()
+    for field, bad in (("level_solver", 2), ("separable_tensor_cores", -1), ("new_shifts_in_levels", 3), ("m", 53),
+                       ("n0", 8), ("inner_restart", 33)):
+        opt = built.sim_default_options(**{field: bad})
+        # the options are checked before the matrices (here: none) and before any device work
+        assert lib.sim_create(None, None, ctypes.byref(opt), None, ctypes.byref(h)) == 1, field
+        assert b"options out of range" in lib.sim_last_error(None), field
+        assert not h.value
+
+
 def test_null_arguments_are_rejected_without_a_gpu(built):
     lib = built.lib()
     h = ctypes.c_void_p()
