@@ -18,9 +18,9 @@
 // MMAs; a smaller launch uses two stages per CTA (staging of the next 32
 // indices while the current ones multiply).  FP32 accuracy from TF32 units:
 // every value is split as x = hi + lo with hi its leading 11 significand bits
-// (exact in TF32), and
-// Y = X_hi Q_hi + X_hi Q_lo + X_lo Q_hi accumulated in FP32 (the dropped
-// X_lo Q_lo term is below FP32 rounding); Q's halves are tables made once.
+// (exact in TF32), and Y = X_hi Q_hi + X_hi Q_lo + X_lo Q_hi accumulated in
+// FP32 (the dropped X_lo Q_lo term is below FP32 rounding); Q's halves are
+// tables made once.
 // One thread issues the MMAs and commits them to the stage's mbarrier; the
 // epilogue reads the accumulator with tcgen05.ld (warp w: lanes 32 (w mod 4) ..,
 // half the columns each) and stores Y.  Every wait has an iteration limit.
