@@ -15,7 +15,9 @@
 // quantities; the Schur form is its unitary, backward-stable counterpart.
 //
 // k_schur: one warp per shift, the shifted QR algorithm of k_ritz applied to
-// whole rows and columns with the rotations accumulated into Z.
+// whole rows and columns with the rotations accumulated into the two rows of Z
+// the level needs (the first and the last: a row of Z evolves on its own
+// under the column rotations).
 // k_eval_schur: one lane per quadrature node (a warp holds the 8 nodes of 4
 // squares), so every FP64 instruction does useful work in all lanes; T's
 // entries are warp-uniform loads when the 4 squares share a shift (children
@@ -45,7 +47,7 @@ __device__ __forceinline__ double2 conj_s(double2 a) { return make_double2(a.x, 
 
 }  // namespace
 
-// Shared memory: A [m][m] and Z [m][m], row-major.
+// Shared memory: A [m][m] row-major, then rows 0 and n-1 of Z.
 __global__ void __launch_bounds__(32) k_schur(const double2* Hall, int m, const int* meff_all, const double* beta_all,
                                               int s0, double2* Tall, double2* Call, double2* Qall, int* ok_all) {
     const int s = s0 + blockIdx.x;
@@ -53,7 +55,8 @@ __global__ void __launch_bounds__(32) k_schur(const double2* Hall, int m, const 
     const double2* Hs = Hall + (size_t)s * (m + 1) * m;  // column-major, leading dimension m + 1
     extern __shared__ double2 sh_schur[];
     double2* A = sh_schur;
-    double2* Z = sh_schur + (size_t)m * m;
+    double2* Z0 = sh_schur + (size_t)m * m;  // row 0 of Z
+    double2* Zl = Z0 + m;                    // row n-1 of Z
     __shared__ double gc[64];
     __shared__ double2 gs[64];
     __shared__ double2 s_mu;
@@ -62,7 +65,10 @@ __global__ void __launch_bounds__(32) k_schur(const double2* Hall, int m, const 
     for (int idx = lane; idx < n * n; idx += 32) {
         const int r = idx / n, c = idx % n;
         A[r * m + c] = (r <= c + 1) ? Hs[(size_t)c * (m + 1) + r] : make_double2(0.0, 0.0);
-        Z[r * m + c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    }
+    for (int c = lane; c < n; c += 32) {
+        Z0[c] = make_double2(c == 0 ? 1.0 : 0.0, 0.0);
+        Zl[c] = make_double2(c == n - 1 ? 1.0 : 0.0, 0.0);
     }
     double nrm = 0.0;
     for (int idx = lane; idx < n * n; idx += 32) nrm = fmax(nrm, cabs_s(A[(idx / n) * m + idx % n]));
@@ -157,10 +163,11 @@ __global__ void __launch_bounds__(32) k_schur(const double2* Hall, int m, const 
                 A[i * m + k] = cadd(make_double2(c * x.x, c * x.y), cmul(conj_s(sn), y));
                 A[i * m + k + 1] = csub(make_double2(c * y.x, c * y.y), cmul(sn, x));
             }
-            for (int i = lane; i < n; i += 32) {
-                const double2 x = Z[i * m + k], y = Z[i * m + k + 1];
-                Z[i * m + k] = cadd(make_double2(c * x.x, c * x.y), cmul(conj_s(sn), y));
-                Z[i * m + k + 1] = csub(make_double2(c * y.x, c * y.y), cmul(sn, x));
+            if (lane < 2) {
+                double2* Zr = lane == 0 ? Z0 : Zl;
+                const double2 x = Zr[k], y = Zr[k + 1];
+                Zr[k] = cadd(make_double2(c * x.x, c * x.y), cmul(conj_s(sn), y));
+                Zr[k + 1] = csub(make_double2(c * y.x, c * y.y), cmul(sn, x));
             }
             __syncwarp();
         }
@@ -175,9 +182,9 @@ __global__ void __launch_bounds__(32) k_schur(const double2* Hall, int m, const 
             T[r * m + c] = c >= r ? A[r * m + c] : make_double2(0.0, 0.0);
         }
         for (int i = lane; i < n; i += 32) {
-            const double2 z0 = Z[i];  // Z[0][i]
+            const double2 z0 = Z0[i];
             Call[(size_t)s * m + i] = make_double2(beta * z0.x, -beta * z0.y);
-            Qall[(size_t)s * m + i] = Z[(n - 1) * m + i];
+            Qall[(size_t)s * m + i] = Zl[i];
         }
     }
     if (lane == 0) ok_all[s] = fail ? 0 : 1;
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(SE_WARPS * 32) k_eval_schur(ShiftTable st, Lev
 void schur_shifts(const double2* H, int m, const int* meff, const double* beta, int s0, int count, double2* T,
                   double2* C, double2* Q, int* ok, cudaStream_t st) {
     if (count <= 0) return;
-    const size_t sm = (size_t)2 * m * m * sizeof(double2);
+    const size_t sm = ((size_t)m * m + 2 * (size_t)m) * sizeof(double2);
     SIM_CUDA(cudaFuncSetAttribute(k_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_schur<<<count, 32, sm, st>>>(H, m, meff, beta, s0, T, C, Q, ok);
     SIM_LAUNCH_CHECK();
