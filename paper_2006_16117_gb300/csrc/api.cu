@@ -407,17 +407,24 @@ ShiftTable shift_table(sim_ctx* h) {
 }
 
 // One evaluation of a level (mode 0): with level_solver 1 the Schur forms
-// evaluate every square against its own shift and the direct evaluation runs
-// only for the squares they leave; with 0 the direct evaluation runs for all.
-// Returns the number of squares evaluated directly.
-int64_t evaluate_level(const ShiftTable& t, LevelArgs la, int level_solver, DeviceArena& ar, int64_t* bsum,
-                       int64_t* tot, cudaStream_t st) {
+// evaluate every square against its own shift, then the squares left against
+// every shift of their pencil (smax: the most shifts a pencil has), and the
+// direct evaluation runs only where a zero pivot or a missing Schur form
+// stops them; with 0 the direct evaluation runs for all.  Returns the number
+// of squares evaluated directly.
+int64_t evaluate_level(const ShiftTable& t, LevelArgs la, int level_solver, int smax, DeviceArena& ar,
+                       int64_t* bsum, int64_t* tot, cudaStream_t st) {
     if (level_solver == 1 && t.schT && la.count > 0) {
         uint8_t* todo = ar.get<uint8_t>("lvl_todo", la.count);
         eval_level_schur(t, la, todo, st);
+        const int64_t left = count_marked(todo, la.count, bsum, tot, ar.host_i64(), st);
+        if (left == 0) return 0;
+        eval_level_schur_retries(t, la, todo, left, smax, ar, st);
+        const int64_t direct = count_marked(todo, la.count, bsum, tot, ar.host_i64(), st);
+        if (direct == 0) return 0;
         la.todo = todo;
         eval_level(t, la, 0, st);
-        return count_marked(todo, la.count, bsum, tot, ar.host_i64(), st);
+        return direct;
     }
     eval_level(t, la, 0, st);
     return la.count;
@@ -1011,7 +1018,7 @@ sim_status sim_solve_level(sim_handle h, int64_t* n_marked, int32_t* done) {
         for (int round = 0;; ++round) {
             SIM_CUDA(cudaMemsetAsync(la.retries, 0, sizeof(unsigned long long), h->st));
             h->stats.direct_level_evaluations +=
-                evaluate_level(shift_table(h), la, h->opt.level_solver, h->arena, bsum, tot, h->st);
+                evaluate_level(shift_table(h), la, h->opt.level_solver, h->S, h->arena, bsum, tot, h->st);
             h->stats.squares_evaluated += N;
             h->stats.unresolvable_last_level = count_marked(flag, N, bsum, tot, h->arena.host_i64(), h->st);
             unsigned long long rt = 0;
@@ -1709,7 +1716,9 @@ sim_status sim_batch_solve_level(sim_batch b, int64_t* n_marked, int32_t* done) 
         int64_t* bsum = b->arena.get<int64_t>("bsum", nbk + 1);
         int64_t* tot = b->arena.get<int64_t>("tot", 1);
         for (int round = 0;; ++round) {
-            evaluate_level(t, la, h0->opt.level_solver, b->arena, bsum, tot, b->st);
+            int smax = 0;
+            for (int p = 0; p < P; ++p) smax = std::max(smax, b->sb[p + 1] - b->sb[p]);
+            evaluate_level(t, la, h0->opt.level_solver, smax, b->arena, bsum, tot, b->st);
             b->squares_evaluated += N;
             if (!h0->opt.new_shifts_in_levels || round >= h0->opt.max_shift_rounds) break;
             const int64_t un = count_marked(flag, N, bsum, tot, b->arena.host_i64(), b->st);

@@ -115,6 +115,12 @@ void schur_shifts(const double2* H, int m, const int* meff, const double* beta, 
 // forms; todo[q] = 1 for the squares left to eval_level (unresolved by their
 // own shift, or a zero pivot / no Schur form), 0 for those written.
 void eval_level_schur(const ShiftTable& st, const LevelArgs& a, uint8_t* todo, cudaStream_t stream);
+// The ntodo squares it left: every shift of their pencil (at most smax) through
+// the Schur forms at once, then the shift the direct evaluation's order would
+// pick; todo[q] stays 1 only where a zero pivot or a missing Schur form needs
+// the direct evaluation.
+void eval_level_schur_retries(const ShiftTable& st, const LevelArgs& a, uint8_t* todo, int64_t ntodo, int smax,
+                              DeviceArena& ar, cudaStream_t stream);
 
 size_t eval_smem_bytes(int m);
 void eval_level(const ShiftTable& st, const LevelArgs& a, int mode, cudaStream_t stream);

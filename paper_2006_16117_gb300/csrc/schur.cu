@@ -194,7 +194,15 @@ __global__ void __launch_bounds__(32) k_schur(const double2* Hall, int m, const 
 // lane in shared memory as [i][lane] (conflict-free 16-byte accesses).
 constexpr int SE_WARPS = 4;
 
-__global__ void __launch_bounds__(SE_WARPS * 32) k_eval_schur(ShiftTable st, LevelArgs a, uint8_t* todo) {
+// ALL = false: item t is square t against its own shift; a square it resolves
+//   gets its results, the others todo[q] = 1.
+// ALL = true: item t = (i, o) is square list[i] against shift lo + o of its
+//   pencil's range [lo, hi), o < smax; the indicator, the largest node
+//   residual and the zero-pivot / no-Schur-form flag go to rind, rrho, rbad.
+template <bool ALL>
+__global__ void __launch_bounds__(SE_WARPS * 32) k_eval_schur(ShiftTable st, LevelArgs a, uint8_t* todo,
+                                                              const int64_t* list, int smax, int64_t nitems,
+                                                              double* rind, double* rrho, uint8_t* rbad) {
     const double2* Tall = st.schT;
     const double2* Call = st.schC;
     const double2* Qall = st.schQ;
@@ -205,14 +213,26 @@ __global__ void __launch_bounds__(SE_WARPS * 32) k_eval_schur(ShiftTable st, Lev
     double2* xs = sh_x + (size_t)warp * m * 32;
     const int j = lane & 7;  // node
     const int64_t nwarps = (int64_t)gridDim.x * SE_WARPS;
-    for (int64_t q0 = ((int64_t)blockIdx.x * SE_WARPS + warp) * 4; q0 < a.count; q0 += nwarps * 4) {
-        const int64_t q = q0 + (lane >> 3);
-        const bool active = q < a.count;
+    for (int64_t t0 = ((int64_t)blockIdx.x * SE_WARPS + warp) * 4; t0 < nitems; t0 += nwarps * 4) {
+        const int64_t t = t0 + (lane >> 3);
+        int64_t q = t;
+        bool active = t < nitems;
         int s = 0, n = 0;
+        if (ALL && active) {
+            q = list[t / smax];
+            int lo = 0, hi = st.S;
+            if (st.pencil_of) {
+                const int p = st.pencil_of[a.sid[q]];
+                lo = st.p_sb[p];
+                hi = st.p_se[p];
+            }
+            s = lo + (int)(t % smax);
+            active = s < hi;
+        }
         double re_lo = a.re_lo, im_lo = a.im_lo, side = a.side;
         bool good = false;
         if (active) {
-            s = a.sid[q];
+            if (!ALL) s = a.sid[q];
             if (st.pencil_of) {
                 const int p = st.pencil_of[s];
                 re_lo = st.p_re_lo[p];
@@ -303,7 +323,13 @@ __global__ void __launch_bounds__(SE_WARPS * 32) k_eval_schur(ShiftTable st, Lev
             rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
             bad |= __shfl_xor_sync(0xffffffffu, bad, o);
         }
-        if (active && j == 0) {
+        if (ALL && t < nitems && j == 0) {
+            const double s8 = sqrt(n8), s4 = sqrt(n4);
+            rind[t] = s4 > 0.0 ? s8 / s4 : (s8 > 0.0 ? INFINITY : 0.0);
+            rrho[t] = active ? rmax : INFINITY;
+            rbad[t] = active ? (uint8_t)bad : (uint8_t)0;
+        }
+        if (!ALL && active && j == 0) {
             const double s8 = sqrt(n8), s4 = sqrt(n4);
             const double ind = s4 > 0.0 ? s8 / s4 : (s8 > 0.0 ? INFINITY : 0.0);
             if (!bad && rmax <= st.eps) {
@@ -327,17 +353,107 @@ void schur_shifts(const double2* H, int m, const int* meff, const double* beta, 
     SIM_LAUNCH_CHECK();
 }
 
+// The squares their own shift left (todo != 0), listed in any order.
+__global__ void k_list_todo(const uint8_t* todo, int64_t count, int64_t* list, unsigned long long* n) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < count && todo[q]) list[atomicAdd(n, 1ull)] = (int64_t)q;
+}
+
+// One thread per listed square: the result the direct evaluation's shift order
+// gives (own shift first, then the others nearest-first by |σ - c|, ties by the
+// lower id; the first that resolves the square is used; if none does, the own
+// shift's indicator and "unresolvable").  A square with any zero pivot or
+// missing Schur form among its shifts stays todo for the direct evaluation.
+__global__ void k_pick_shift(ShiftTable st, LevelArgs a, const int64_t* list, int64_t ntodo, int smax,
+                             const double* rind, const double* rrho, const uint8_t* rbad, uint8_t* todo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntodo) return;
+    const int64_t q = list[i];
+    const int own = a.sid[q];
+    int lo = 0, hi = st.S;
+    double re_lo = a.re_lo, im_lo = a.im_lo, side = a.side;
+    if (st.pencil_of) {
+        const int p = st.pencil_of[own];
+        lo = st.p_sb[p];
+        hi = st.p_se[p];
+        re_lo = st.p_re_lo[p];
+        im_lo = st.p_im_lo[p];
+        side = st.p_side[p];
+    }
+    const int64_t r0 = i * (int64_t)smax;
+    for (int s = lo; s < hi; ++s)
+        if (rbad[r0 + (s - lo)]) return;  // left to the direct evaluation
+    const double2 c = square_center(re_lo, im_lo, side, a.ix[q], a.iy[q]);
+    int used = own, tried = 1;
+    bool res = rrho[r0 + (own - lo)] <= st.eps;
+    if (!res) {
+        double bd = INFINITY;
+        int best = -1;
+        for (int s = lo; s < hi; ++s) {
+            if (s == own || !(rrho[r0 + (s - lo)] <= st.eps)) continue;
+            const double d = hypot(st.sigma[s].x - c.x, st.sigma[s].y - c.y);
+            if (d < bd || (d == bd && s < best)) {
+                bd = d;
+                best = s;
+            }
+        }
+        if (best >= 0) {
+            res = true;
+            used = best;
+            for (int s = lo; s < hi; ++s) {
+                if (s == own) continue;
+                const double d = hypot(st.sigma[s].x - c.x, st.sigma[s].y - c.y);
+                if (d < bd || (d == bd && s <= best)) ++tried;
+            }
+        } else {
+            tried = hi - lo;
+        }
+    }
+    if (a.retries && tried > 1) atomicAdd(a.retries, (unsigned long long)(tried - 1));
+    const double ind = res ? rind[r0 + (used - lo)] : rind[r0 + (own - lo)];
+    a.ind[q] = ind;
+    a.mark[q] = res ? (ind > st.delta0 ? 1 : 0) : 1;
+    a.flag[q] = res ? 0 : 1;
+    a.sid[q] = used;
+    todo[q] = 0;
+}
+
 void eval_level_schur(const ShiftTable& st, const LevelArgs& a, uint8_t* todo, cudaStream_t stream) {
     if (a.count <= 0) return;
     const size_t sm = (size_t)SE_WARPS * st.m * 32 * sizeof(double2);
-    SIM_CUDA(cudaFuncSetAttribute(k_eval_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SIM_CUDA(cudaFuncSetAttribute(k_eval_schur<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int64_t warps = (a.count + 3) / 4;
     const int grid = (int)std::min<int64_t>((warps + SE_WARPS - 1) / SE_WARPS, 152 * 16);
     kprof_begin("eval_level_schur", stream);
-    k_eval_schur<<<grid, SE_WARPS * 32, sm, stream>>>(st, a, todo);
+    k_eval_schur<false><<<grid, SE_WARPS * 32, sm, stream>>>(st, a, todo, nullptr, 1, a.count, nullptr, nullptr,
+                                                             nullptr);
     SIM_LAUNCH_CHECK();
     // per square: 8 triangular solves of order m (m²/2 complex multiply-adds each)
     kprof_end("eval_level_schur", stream, 0.0, a.count * 8.0 * 4.0 * st.m * st.m);
+}
+
+void eval_level_schur_retries(const ShiftTable& st, const LevelArgs& a, uint8_t* todo, int64_t ntodo, int smax,
+                              DeviceArena& ar, cudaStream_t stream) {
+    if (ntodo <= 0 || smax <= 0) return;
+    int64_t* list = ar.get<int64_t>("lvl_list", ntodo);
+    unsigned long long* cnt = ar.get<unsigned long long>("lvl_list_n", 1);
+    const int64_t nitems = ntodo * (int64_t)smax;
+    double* rind = ar.get<double>("lvl_rind", nitems);
+    double* rrho = ar.get<double>("lvl_rrho", nitems);
+    uint8_t* rbad = ar.get<uint8_t>("lvl_rbad", nitems);
+    SIM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), stream));
+    k_list_todo<<<cdiv_up(a.count, 256), 256, 0, stream>>>(todo, a.count, list, cnt);
+    SIM_LAUNCH_CHECK();
+    const size_t sm = (size_t)SE_WARPS * st.m * 32 * sizeof(double2);
+    SIM_CUDA(cudaFuncSetAttribute(k_eval_schur<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int64_t warps = (nitems + 3) / 4;
+    const int grid = (int)std::min<int64_t>((warps + SE_WARPS - 1) / SE_WARPS, 152 * 16);
+    kprof_begin("eval_level_schur", stream);
+    k_eval_schur<true><<<grid, SE_WARPS * 32, sm, stream>>>(st, a, todo, list, smax, nitems, rind, rrho, rbad);
+    SIM_LAUNCH_CHECK();
+    k_pick_shift<<<cdiv_up(ntodo, 128), 128, 0, stream>>>(st, a, list, ntodo, smax, rind, rrho, rbad, todo);
+    SIM_LAUNCH_CHECK();
+    kprof_end("eval_level_schur", stream, 0.0, nitems * 8.0 * 4.0 * st.m * st.m);
 }
 
 }  // namespace sim

@@ -211,8 +211,9 @@ def test_schur_level_solver_equals_direct_solves(simlib, case):
     """level_solver 1 (Schur form of H_m per shift, one triangular solve per
     node, Sec. 3.2) and level_solver 0 (Gaussian elimination of I + (σ - z)H_m
     at every node) evaluate the same quantities: the same squares are marked at
-    every level and the located eigenvalues are the same square centres.  The
-    Schur path leaves only the squares their own shift does not resolve."""
+    every level, the located eigenvalues are the same square centres and the
+    shift retries are the same (the Schur path evaluates a square its own shift
+    leaves against every shift and picks the one the direct order would)."""
     import scipy.linalg as sla
 
     from workloads import cd2d_csr, config_jordan_small, config_small, diag_csr
