@@ -158,6 +158,15 @@ def test_residual_formula_equals_explicit_residual():
         e = np.zeros(m, complex)
         e[0] = ks.beta
         assert np.linalg.norm(T @ y[q] - e) < 1e-10 * ks.beta
+    # the other reading of the test (option residual_scale = "beta"): the same
+    # solve, the explicit residual relative to the right-hand side's norm β
+    yb, rho_b = S.projected_solve(ks, z, "beta")
+    assert np.array_equal(yb, y)
+    for q, zq in enumerate(z):
+        x = ks.V[:, :m] @ y[q]
+        r = b - (x + (sigma - zq) * (M @ x))
+        explicit = np.linalg.norm(r) / np.linalg.norm(b)
+        assert abs(explicit - rho_b[q]) <= 1e-7 * explicit + 1e-12
 
 
 def test_tiling_and_levels():
