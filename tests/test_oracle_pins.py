@@ -481,3 +481,51 @@ def test_eig_decomposition_screen_equals_direct_solve():
     # and the decomposition reproduces H_m
     m = ks.m_eff
     assert np.linalg.norm(P @ np.diag(d) @ np.linalg.inv(P) - ks.H[:m, :m]) <= 1e-9 * np.linalg.norm(ks.H[:m, :m])
+
+
+def test_schur_form_evaluation_equals_direct_solve():
+    """The identities the levels' Schur path uses (Sec. 3.2 with the unitary
+    H_m = Z T Z^H in place of P D P^{-1}), on a non-normal pencil's Krylov
+    space: x = (I + αT)^{-1} β Z^H e_1 gives ||x|| = ||y||, z_m^T x = e_m^T y, and
+    the indicator and residuals of whole squares equal the oracle's direct
+    evaluation (scipy's complex Schur form serves as the library step)."""
+    import scipy.linalg as sla
+
+    from workloads import cd2d_csr
+
+    A = cd2d_csr(20, (1.0, 0.5)).to_scipy()
+    n = A.shape[0]
+    f = np.random.default_rng(9).standard_normal(n) + 1j * np.random.default_rng(10).standard_normal(n)
+    sigma = 400.0 + 0.2j
+    ks = S.cayley_arnoldi(A, sp.identity(n, dtype=complex, format="csr"), sigma, f, 20)
+    m = ks.m_eff
+    H = ks.H[:m, :m]
+    T, Z = sla.schur(H, output="complex")
+    assert np.linalg.norm(Z @ T @ Z.conj().T - H) <= 1e-12 * np.linalg.norm(H)
+    c = ks.beta * Z[0, :].conj()
+    rng = np.random.default_rng(11)
+    centers = sigma + rng.uniform(-300, 300, 12) + 1j * rng.uniform(-1, 1, 12)
+    sides = rng.uniform(0.05, 2.0, 12)
+    ind_direct, rmax_direct = S.evaluate_squares(ks, centers, sides)
+    hlast = abs(ks.H[m, m - 1])
+    for q in range(centers.size):
+        off = S.node_offsets(np.array(sides[q]))
+        z = centers[q] + off
+        y, _ = S.projected_solve(ks, z)
+        xs = []
+        rho = []
+        for j in range(8):
+            alpha = sigma - z[j]
+            x = sla.solve_triangular(np.eye(m) + alpha * T, c)
+            assert abs(np.linalg.norm(x) - np.linalg.norm(y[j])) <= 1e-9 * np.linalg.norm(y[j])
+            last = Z[m - 1, :] @ x
+            assert abs(last - y[j][m - 1]) <= 1e-9 * np.linalg.norm(y[j])
+            rho.append(abs(alpha) * hlast * abs(last) / np.linalg.norm(x))
+            xs.append(x)
+        xs = np.array(xs)
+        s8 = np.linalg.norm(np.sum((off / 8.0)[:, None] * xs, axis=0))
+        s4 = np.linalg.norm(np.sum((off[0::2] / 4.0)[:, None] * xs[0::2], axis=0))
+        assert abs(s8 / s4 - ind_direct[q]) <= 1e-8 * max(1.0, ind_direct[q])
+        # residuals agree to rounding (an absolute floor far below ε = 1e-8)
+        assert abs(max(rho) - rmax_direct[q]) <= 1e-6 * rmax_direct[q] + 1e-13
+    assert np.max(rmax_direct) > 1e-6  # the 20-dimensional space is not exact for every square
