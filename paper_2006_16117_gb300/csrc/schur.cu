@@ -21,9 +21,11 @@
 // k_eval_schur: one lane per quadrature node (a warp holds the 8 nodes of 4
 // squares), so every FP64 instruction does useful work in all lanes; T's
 // entries are warp-uniform loads when the 4 squares share a shift (children
-// of one square do).  A square whose own shift does not resolve it, or whose
-// evaluation meets a zero pivot or a shift without a Schur form, is left to the
-// direct evaluation (k_eval_level), which then tries the shifts in order.
+// of one square do).  The squares their own shift does not resolve are then
+// evaluated against every shift of their pencil at once (square-shift pairs
+// as items) and k_pick_shift takes the shift the direct evaluation's order
+// would.  Only a zero pivot or a shift without a Schur form sends a square to
+// the direct evaluation (k_eval_level).
 #include <cfloat>
 
 #include "hess.cuh"
