@@ -5,7 +5,8 @@
 // device-side compaction, and the merge of the final squares into clusters
 // (Sec. 3.5 step 6).
 //
-// Projected solve: one warp per quadrature node.  T = I + (σ - z) H_m is upper
+// Direct projected solve (option level_solver 0, and the squares the Schur
+// path of schur.cu cannot take): one warp per quadrature node.  T = I + (σ - z) H_m is upper
 // Hessenberg, so Gaussian elimination with partial pivoting only ever compares
 // the carried pivot row with the next original row; the warp keeps the carried
 // row in registers (two columns per lane), writes the rows of U to shared
